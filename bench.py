@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Mu3e online event selection on GB300.
+
+Workload (one step): the full-rate batch of 1,000,000 synthetic frames per GPU
+(Poisson(20) tracks per frame, 2 noise hits per layer, a signal decay in 0.1 % of
+the frames, seed 2 on rank 0), int32 pixel addresses resident in HBM (343 MB,
+larger than L2, so no flush is needed between steps).  A step is one
+m3e_select_frames call over the whole batch: every stage of the method runs in
+the library's kernels.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s and hits/s per GB300 vs plain per-frame form; % issue roofline; p99 latency"
+WORKLOAD = ("full-rate throughput: 1,000,000 frames per GPU, Poisson(20) tracks/frame (p 15-53 MeV, "
+            "|cos theta| < 0.8, double-cone target), 2 noise hits/layer, signal decay in 0.1% of frames, "
+            "4 layers r=25/31/73/85 mm, B=1 T, 80 um pixels, int32 addresses")
+# Arithmetic operations per work item of the method's formulas (FMA = 2, each
+# transcendental, division or square root = 1); see DESIGN.md "Roofline".
+OPS_PER_ITEM = {"pair_tests": 4, "triplet_tests": 6, "triplets": 460, "energy_tests": 7, "vertexed": 640}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def shard_seed(rank: int) -> int:
+    """Weak scaling: rank r selects its own batch (seed 2 on rank 0)."""
+    return 2 + 7919 * rank
+
+
+def make_batch(n_frames: int, rank: int):
+    from paper_2206_11535_gb300 import gen
+    return gen.generate(n_frames, 20.0, 2.0, 1000, seed=shard_seed(rank))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 8:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = np.array([float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()])
+        mx = max(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm.size else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("m3e_kernels.cu", "m3e_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2206_11535_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n_frames: int):
+    """DRAM bytes per launch of the persistent kernel from the committed ncu summary,
+    scaled to n_frames; None when the summary was taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", "select_warp_c2_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_frame"]) * n_frames
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(d, seconds_target=12.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded prefix of the batch."""
+    from oracle import oracle as O
+    from paper_2206_11535_gb300 import gen
+    c = O.make_config(gen.load_config())
+    cores = os.cpu_count() or 1
+    nf = d["off"].size - 1
+    # calibrate the sample size on a small prefix, then time a prefix worth ~seconds_target
+    n0 = min(2000, nf)
+    t = time.perf_counter()
+    O.select_frames(c, d["hits"], d["off"][:n0 + 1], cores)
+    rate0 = n0 / max(time.perf_counter() - t, 1e-6)
+    n = int(min(nf, max(n0, rate0 * seconds_target)))
+    t = time.perf_counter()
+    O.select_frames(c, d["hits"], d["off"][:n + 1], cores)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n} frames of the rank-0 batch, FP64 C oracle (-O2), {cores} threads over "
+                      f"disjoint frame ranges, brute force over every hit triplet ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2206_11535_gb300 import gen
+    O.build()
+    c = O.make_config(gen.load_config())
+    cores = os.cpu_count() or 1
+    n = min(args.frames, 20000)
+    d = make_batch(n, 0)
+    for _ in range(args.warmup):
+        O.select_frames(c, d["hits"], d["off"], cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        O.select_frames(c, d["hits"], d["off"], cores)
+    dt = time.perf_counter() - t
+    v = n * args.steps / dt
+    sample = (f"{n} frames of the rank-0 batch per step (bounded sample of the 1,000,000-frame workload), "
+              f"FP64 C oracle, {cores} threads")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD, "frames_per_step": n},
+                      "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2206_11535_gb300 import gen, m3e
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = gen.load_config()
+    d = make_batch(args.frames, rank)
+    nf = d["off"].size - 1
+    nh = int(d["off"][-1])
+    dev = torch.device("cuda", local)
+    hits = torch.from_numpy(d["hits"]).to(dev)
+    off = torch.from_numpy(d["off"]).to(dev)
+    keep = torch.empty(nf, dtype=torch.uint8, device=dev)
+    reason = torch.empty(nf, dtype=torch.uint8, device=dev)
+    ctx = m3e.Context(cfg, local)
+    stream = torch.cuda.current_stream(dev)
+
+    # work counts of this batch (untimed) for the algorithmic operation count
+    st = m3e.new_stats(dev)
+    ctx.select_frames(hits, off, keep, reason, stats=st)
+    torch.cuda.synchronize()
+    stats = m3e.stats_dict(st)
+    ctx.check()
+
+    def timed(fn, steps, warm, profile=False):
+        for _ in range(warm):
+            fn()
+        barrier()
+        ks = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+            if profile:
+                ks.append(ctx.kernel_times())
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, ks
+
+    # main arm: persistent kernel, kernel durations recorded on the launching stream
+    ctx.set_profiling(True)
+    with Clocks(local) as clk:
+        ms, ks = timed(lambda: ctx.select_frames(hits, off, keep, reason, stream=stream), args.steps,
+                       args.warmup, profile=True)
+    launches = ctx.last_launch_count() * args.steps
+    ctx.set_profiling(False)
+    # plain per-frame form, same batch
+    ms_plain, _ = timed(lambda: ctx.select_frames_plain(hits, off, keep, reason, stream=stream),
+                        max(2, args.steps // 2), 1)
+    plain_steps = max(2, args.steps // 2)
+    # end to end from pinned host memory through the C ABI host entry point
+    e2e = None
+    if not args.no_e2e:
+        hh = torch.from_numpy(d["hits"]).pin_memory()
+        ho = torch.from_numpy(d["off"]).pin_memory()
+        hk = torch.empty(nf, dtype=torch.uint8).pin_memory()
+        hr = torch.empty(nf, dtype=torch.uint8).pin_memory()
+        ms_e2e, _ = timed(lambda: ctx.select_frames_host(hh, ho, hk, hr, stream=stream), args.steps, args.warmup)
+        e2e = {"value": world * nf * args.steps / (ms_e2e / 1e3), "unit": "frames/s",
+               "h2d_bytes_per_step": int(hh.numel() * 4 + ho.numel() * 8), "d2h_bytes_per_step": int(2 * nf),
+               "ms_per_step": ms_e2e / args.steps}
+    ctx.check()
+
+    value = world * nf * args.steps / (ms / 1e3)
+    kmain = float(np.mean([k[0] for k in ks])) if ks else float("nan")
+    kdef = float(np.mean([k[1] for k in ks])) if ks else float("nan")
+    props = torch.cuda.get_device_properties(dev)
+    cl = clk.summary()
+    f_mhz = cl["sm_mhz"] or 1455.0
+    ops = sum(stats[k] * v for k, v in OPS_PER_ITEM.items())
+    achieved = ops / (kmain / 1e3) / 1e12
+    peak = props.multi_processor_count * 128 * 2 * f_mhz * 1e6 / 1e12
+    tr = recorded_traffic(nf)
+    roof = {"bound": "alu", "kernel": "k_select_warp (persistent warp-per-frame selection)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": tr, "kernel_ms": kmain, "deferred_kernel_ms": kdef,
+            "ops_per_launch": ops, "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf,
+            "hbm_gbs_at_kernel_time": (nh * 4 + (nf + 1) * 8 + 2 * nf) / (kmain / 1e3) / 1e9,
+            "peak_source": f"FP32 lanes x 2 x SM clock: {props.multi_processor_count} SMs x 128 x 2 x "
+                           f"{f_mhz:.0f} MHz (median sampled under load)"}
+    out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "frames_per_gpu": nf, "hits_per_gpu": nh,
+                      "l2": "inputs larger than L2 (no flush)", "form": "persistent warp-per-frame, device queue",
+                      "parallelism": f"{world} independent GPU shard(s), no collective on the data path"},
+           "hits_per_s": world * nh * args.steps / (ms / 1e3),
+           "plain_per_frame": {"value": world * nf * plain_steps / (ms_plain / 1e3), "unit": "frames/s",
+                               "ms_per_step": ms_plain / plain_steps,
+                               "speedup_of_persistent": (ms_plain / plain_steps) / (ms / args.steps)},
+           "kept_fraction": float(keep.float().mean().item()),
+           "reasons": dict(zip(m3e.REASONS, stats["reasons"][:7])),
+           "roofline": roof, "e2e": e2e, "clocks": cl, "gpu_launches": launches}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(d)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

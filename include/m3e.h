@@ -1,0 +1,188 @@
+/* m3e: GB300-native Mu3e online event selection (arXiv:2206.11535).
+ *
+ * The problem statement is the paper's (Sec. "Online Event Selection",
+ * Sec. "Implementation"): a batch of frames of detector hits goes in, and one
+ * keep/drop decision per frame comes out.  Per frame the library runs the three
+ * steps of the paper: the selection cuts on hit triplets of layers 0-2
+ * (Sec. "Selection Cuts", Algorithm 2), the triplet-fit track reconstruction
+ * with the fourth layer and a chi2 < 32 cut (Sec. "Track Reconstruction",
+ * Algorithm 3) and the geometric e+ e+ e- vertex selection (Sec. "Vertex Fit",
+ * Algorithm 4).  Frames whose candidate lists overflow the caps are kept
+ * unprocessed (Algorithms 2-4).
+ *
+ * Conventions of every entry point:
+ *   - Return value: M3E_OK (0) or a negative M3E_E* code; the message of the
+ *     last failure of the calling thread is m3e_last_error_string().
+ *   - Pointers named d_* are DEVICE pointers owned by the caller, on the
+ *     context's device; h_* are HOST pointers owned by the caller (pinned memory
+ *     gives overlapped copies, pageable memory still works).
+ *   - Work is enqueued asynchronously on the caller's stream; no call
+ *     synchronises the device.  Results are valid once the stream has reached
+ *     the call.  The context allocates only its own scratch (look-up tables,
+ *     work queue, deferred-frame list, staging buffers of the host entry point).
+ *   - A context is not safe for concurrent use by several host threads.
+ *
+ * Input format.  Frame f owns hits[frame_off[f] .. frame_off[f+1]) of a CSR
+ * batch; frame_off has n_frames + 1 entries, non-decreasing.  A hit is a packed
+ * int32 pixel address:
+ *   bits [31:28] zero, [27:26] layer 0..3, [25:21] ladder, [20:13] column,
+ *   [12:0] row.
+ * Global column g = ladder * n_cols[layer] + column counts around the cylinder
+ * from phi = 0; the pixel centre is (r cos phi, r sin phi, -H + (row + 1/2) pitch)
+ * with phi = (g + 1/2) 2 pi / (n_ladders n_cols) (the paper's detector model of
+ * four concentric cylinders, Sec. "Selection Cuts").  The hit order inside a
+ * frame is arbitrary and does not change any result; duplicate addresses are
+ * distinct hits.
+ *
+ * Output.  keep[f] is 1 for a frame to store, 0 to drop; reason[f] is one of
+ * enum m3e_reason.  A frame holding an address outside the detector (or a
+ * negative size) is kept with reason M3E_ERR_BADHIT and M3E_EBADHIT is latched
+ * in the context (read it with m3e_check).
+ */
+#ifndef M3E_H
+#define M3E_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define M3E_VERSION 100
+
+enum m3e_status {
+  M3E_OK = 0,
+  M3E_EINVAL = -1,    /* bad argument or configuration */
+  M3E_ENOMEM = -2,    /* device or host allocation failed */
+  M3E_EBADHIT = -3,   /* a frame held an invalid pixel address (latched, see m3e_check) */
+  M3E_ECUDA = -4,     /* a CUDA runtime call failed */
+  M3E_EBUSY = -5,     /* admission refused (streaming) */
+  M3E_ETIMEOUT = -6,  /* a bounded device wait expired */
+  M3E_ESTATE = -7     /* call not valid in the context's current state */
+};
+
+enum m3e_reason {
+  M3E_DROP = 0,             /* no signal-like vertex: drop the frame */
+  M3E_VERTEX = 1,           /* an e+ e+ e- combination passed the vertex cuts */
+  M3E_TRIPLET_OVERFLOW = 2, /* more than max_triplets selected triplets */
+  M3E_TRACK_OVERFLOW = 3,   /* more than max_tracks tracks */
+  M3E_COMBO_OVERFLOW = 4,   /* more than max_combos combinations passed the energy test */
+  M3E_HIT_OVERFLOW = 5,     /* more than max_hits hits (staging capacity) */
+  M3E_ERR_BADHIT = 6        /* invalid address or frame size */
+};
+
+/* Parameters.  Units mm, MeV, T, rad.  Plain data, versioned by its size. */
+typedef struct {
+  uint32_t size;                     /* must be sizeof(m3e_config) */
+  double r_mm[4], half_len_mm[4];    /* layer radii and half lengths */
+  int32_t n_ladders[4], n_cols[4], n_rows[4];
+  double pitch_mm;
+  double B_T, field_scale;           /* solenoid field along +z and its scale */
+  double x_over_X0[4];               /* material per layer crossing (Highland width) */
+  double k_MeV_per_T_mm, m_mu_MeV, m_e_MeV;
+  double target_r_mm, target_half_len_mm;  /* hollow double-cone target */
+  /* selection cuts (Sec. "Selection Cuts"), inclusive */
+  double dlambda_max, phi01_max, phi12_max, rtc_min, rtc_max;
+  double chi2_track_max;             /* strict: keep chi2 < chi2_track_max (32 in the paper) */
+  /* vertex cuts (Sec. "Vertex Fit"), inclusive */
+  double e_window, isect_margin, vtx_chi2_max, target_dist_max, ptot_max;
+  int32_t max_hits;                  /* <= 4096 */
+  int32_t max_triplets;              /* <= 1024 (768 in the paper) */
+  int32_t max_tracks;                /* <= 128 */
+  int32_t max_combos;                /* <= 1024 */
+} m3e_config;
+
+/* Per-batch counters, accumulated by atomics into caller-owned DEVICE memory
+ * that the caller zeroes.  Work counts are per-frame sums. */
+typedef struct {
+  unsigned long long frames, hits;
+  unsigned long long pair_tests;     /* Phi tests of layer-0/1 and layer-1/2 hit pairs */
+  unsigned long long triplet_tests;  /* Delta-lambda tests after both Phi cuts */
+  unsigned long long triplets;       /* selected triplets (fits run) */
+  unsigned long long tracks;         /* tracks kept by the chi2 cut */
+  unsigned long long energy_tests;   /* e+ e+ e- combinations tested for energy */
+  unsigned long long combos;         /* combinations passing the energy test */
+  unsigned long long vertexed;       /* combinations vertexed */
+  unsigned long long deferred;       /* frames re-run by the large-frame path */
+  unsigned long long reasons[8];     /* frames per m3e_reason */
+} m3e_stats;
+
+/* Optional per-frame record of the candidates (parity checks and debugging):
+ * caller-owned DEVICE arrays, frame f at offset f * cap.  Hit indices are INPUT
+ * indices, the position of the hit within its frame's packet. */
+typedef struct {
+  int32_t cap_trip;        /* records kept per frame for triplets (<= max_triplets) */
+  int32_t cap_combo;       /* records kept per frame for combinations (<= max_combos) */
+  int32_t* n_trip;         /* [F] selected triplets (full count) */
+  int32_t* trip;           /* [F][cap_trip][4] i0, i1, i2, i3 (i3 = -1 when no 4th hit) */
+  int32_t* trk_status;     /* [F][cap_trip] 0 fit1 invalid, 1 no layer-3 crossing, 2 no layer-3
+                              hit, 3 fit2 invalid, 4 chi2 >= cut, 5 kept */
+  float* trk_val;          /* [F][cap_trip][4] kappa_bar, theta01, chi2, 4th-hit metric */
+  int32_t* n_combo;        /* [F] combinations passing the energy test (full count) */
+  int32_t* combo;          /* [F][cap_combo][4] triplet record index of e+, e+, e-, and
+                              status | pass << 8 (status 0 no intersection, 1 emptied by the
+                              target filter, 2 vertexed) */
+  float* combo_val;        /* [F][cap_combo][4] energy sum - m_mu, chi2, target distance, |sum p| */
+} m3e_dump;
+
+typedef struct m3e_ctx m3e_ctx;
+
+/* Create a context on CUDA device cuda_device: checks the configuration, builds
+ * the pixel look-up tables in FP64 (rounded once to FP32) and uploads them. */
+int m3e_create(const m3e_config* cfg, int cuda_device, m3e_ctx** out);
+
+/* Release the context and its device memory (synchronises the context's device). */
+int m3e_destroy(m3e_ctx* ctx);
+
+/* Select frames (the whole method of the paper, every step in CUDA kernels):
+ * persistent warp-per-frame kernel over a device work queue, frames too large
+ * for a warp's shared-memory stage re-run by a CTA-per-frame kernel.
+ * d_stats may be NULL.  n_frames may be 0. */
+int m3e_select_frames(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                      uint8_t* d_keep, uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t stream);
+
+/* The same decisions through the plain per-frame form: one CTA per frame, one
+ * launch per batch (the layout of the paper's main kernel, Algorithm 1). */
+int m3e_select_frames_plain(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                            uint8_t* d_keep, uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t stream);
+
+/* m3e_select_frames with the candidate record filled in; the vertex stage then
+ * evaluates every combination instead of stopping at the first passing one. */
+int m3e_select_frames_debug(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                            uint8_t* d_keep, uint8_t* d_reason, const m3e_dump* dump, cudaStream_t stream);
+
+/* End to end from HOST memory: copies the hits and offsets to the device in
+ * chunks, selects, and copies keep/reason back, overlapping the copies of one
+ * chunk with the kernels of another on two internal streams.  Returns after
+ * enqueueing; the results are in h_keep/h_reason once `stream` has reached the
+ * call (the caller's stream waits for both internal streams). */
+int m3e_select_frames_host(m3e_ctx* ctx, const int32_t* h_hits, const int64_t* h_frame_off, int64_t n_frames,
+                           uint8_t* h_keep, uint8_t* h_reason, cudaStream_t stream);
+
+/* Synchronise `stream` and return M3E_EBADHIT if any earlier call saw an invalid
+ * address or frame size (and clear the latch), else M3E_OK. */
+int m3e_check(m3e_ctx* ctx, cudaStream_t stream);
+
+/* Tuning of the persistent kernel: frames taken per work-queue grab (1..64) and
+ * resident CTAs per SM (0 = as many as fit). */
+int m3e_set_launch(m3e_ctx* ctx, int frames_per_grab, int ctas_per_sm);
+
+/* Number of kernel launches the last select call enqueued. */
+int m3e_last_launch_count(const m3e_ctx* ctx);
+
+/* Kernel timing.  With on = 1, each m3e_select_frames / _plain call records CUDA
+ * events on the caller's stream around each of its kernels.  m3e_kernel_times
+ * waits for the events of the last call and returns the duration in ms of the
+ * main kernel (persistent warp kernel, or the plain CTA kernel) and of the
+ * deferred-frame kernel (0 for the plain form).  Timing adds no device sync. */
+int m3e_set_profiling(m3e_ctx* ctx, int on);
+int m3e_kernel_times(m3e_ctx* ctx, float* main_ms, float* deferred_ms);
+
+const char* m3e_last_error_string(void);
+int m3e_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

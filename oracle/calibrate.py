@@ -69,18 +69,49 @@ def truth_triplet_vars(c, d):
     return np.array(vs)
 
 
+def all_triplet_vars(c, d, n_frames):
+    """Cut variables of every layer-0/1/2 combination of the first frames (fills the
+    lattice of values that digitised hits can produce)."""
+    out = []
+    for f in range(n_frames):
+        a, b = d["off"][f], d["off"][f + 1]
+        lay = d["hit_layer"][a:b]
+        pos = _positions(c, d["hits"][a:b])
+        for i0 in np.nonzero(lay == 0)[0]:
+            for i1 in np.nonzero(lay == 1)[0]:
+                for i2 in np.nonzero(lay == 2)[0]:
+                    out.append(O.cut_vars(c, pos[i0], pos[i1], pos[i2]))
+    return np.array(out)
+
+
+def off_lattice(thr, values, upward):
+    """Digitised hits make the cut variables take discrete values (Delta lambda lives
+    on a lattice of step pitch / (r2 - r1)), and a quantile lands on one of them.  Move
+    the threshold halfway to the next distinct value beyond it, so that no achievable
+    value sits on the threshold and the decision never hangs on rounding."""
+    u = np.unique(np.round(values, 9))  # one entry per lattice point despite rounding
+    t = round(float(thr), 9)
+    nxt = u[u > t] if upward else u[u < t][::-1]
+    return float(0.5 * (thr + nxt[0])) if nxt.size else float(thr)
+
+
 def calibrate_selection(cfg):
     c = O.make_config(cfg)
     d = gen.generate(4000, 10.0, 0.5, 10, seed=SEED)
     v = truth_triplet_vars(c, d)
+    w = all_triplet_vars(c, d, 200)
     q = Q_SEL
     cuts = cfg["cuts"]
-    cuts["dlambda_max"] = float(np.quantile(np.abs(v[:, 0]), q))
-    cuts["phi01_max"] = float(np.quantile(np.arccos(np.clip(v[:, 1], -1, 1)), q))
-    cuts["phi12_max"] = float(np.quantile(np.arccos(np.clip(v[:, 2], -1, 1)), q))
+    cuts["dlambda_max"] = off_lattice(np.quantile(np.abs(v[:, 0]), q), np.abs(np.r_[v[:, 0], w[:, 0]]), True)
+    ph01 = np.arccos(np.clip(np.r_[v[:, 1], w[:, 1]], -1, 1))
+    ph12 = np.arccos(np.clip(np.r_[v[:, 2], w[:, 2]], -1, 1))
+    cuts["phi01_max"] = off_lattice(np.quantile(np.arccos(np.clip(v[:, 1], -1, 1)), q), ph01, True)
+    cuts["phi12_max"] = off_lattice(np.quantile(np.arccos(np.clip(v[:, 2], -1, 1)), q), ph12, True)
     r = np.abs(v[:, 3])
-    cuts["rtc_min"] = float(np.quantile(r, (1 - q) / 2))
-    cuts["rtc_max"] = float(np.quantile(r, 1 - (1 - q) / 2))
+    rall = np.abs(np.r_[v[:, 3], w[:, 3]])
+    rall = rall[np.isfinite(rall)]
+    cuts["rtc_min"] = off_lattice(np.quantile(r, (1 - q) / 2), rall, False)
+    cuts["rtc_max"] = off_lattice(np.quantile(r, 1 - (1 - q) / 2), rall, True)
     return cfg
 
 
@@ -174,7 +205,7 @@ def main():
     if args.write:
         for k, v in cfg["cuts"].items():
             if isinstance(v, float):
-                cfg["cuts"][k] = float("%.6g" % v)
+                cfg["cuts"][k] = float("%.9g" % v)
         with open(gen.config_path(), "w") as f:
             json.dump(cfg, f, indent=2)
             f.write("\n")

@@ -1,0 +1,75 @@
+// Internal definitions shared by the kernels and the C ABI of libm3e.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "m3e.h"
+
+namespace m3e {
+
+constexpr int NB = 32;            // phi bins per layer (power of two)
+constexpr int NBK = 4 * NB;       // (layer, bin) buckets
+constexpr int DEFERRED = -1;      // process_frame result: frame too large for the warp stage
+
+// Shared-memory capacities of the two frame stages.  The warp stage holds
+// typical frames; anything above its capacities is re-run by the CTA stage,
+// whose capacities are the configuration limits.
+constexpr int W_HITS = 160, W_TRIP = 160, W_TRK = 48, W_COMBO = 512;
+constexpr int C_HITS = 4096, C_TRIP = 1024, C_TRK = 128, C_COMBO = 1024;
+constexpr int WARPS_PER_CTA = 4;  // persistent warp kernel: warps (frames in flight) per CTA
+constexpr int CTA_THREADS = 256;  // large-frame kernel
+constexpr int PLAIN_THREADS = 128;  // plain per-frame kernel
+
+// Geometry and cuts, precomputed on the host in FP64 and rounded once.
+struct DevCfg {
+  float r[4];
+  float inv_dr01, inv_dr12;   // 1/(r1 - r0), 1/(r2 - r1), nominal radii
+  float c01, c12;             // cos(phi_max) * r_i * r_j: a pair passes when h_i . h_j >= c
+  float dl_max;               // |Delta lambda| <= dl_max
+  float rtc_lo2, rtc_hi2;     // (2 rtc_min)^2, (2 rtc_max)^2 against (d01 d12 d20)^2 / cross^2
+  int k01, k12;               // phi-bin half windows of the two pair cuts
+  int ntot[4], ncol[4], nlad[4], nrow[4];
+  int col_off[4], row_off[4]; // offsets of each layer in the look-up tables
+  float kB;                   // p [MeV] = kB * R [mm]
+  float hl[4];                // Highland width numerator: sigma_MS(p) = hl[layer] / p
+  float chi2_trk;
+  float r3;
+  float me2, m_mu, e_win;
+  float isect_lim;            // target_r + isect_margin
+  float tgt_r, tgt_h, vtx_chi2, tgt_dist, ptot_max;
+  float sig_pix2;             // pitch^2 / 12
+  int max_hits, max_trip, max_trk, max_combo;
+};
+
+struct KParams {
+  const int32_t* hits;
+  const int64_t* off;
+  int64_t n_frames;
+  int64_t off_base;           // subtracted from off[] (chunked host entry point)
+  uint8_t* keep;
+  uint8_t* reason;
+  unsigned long long* stats;  // m3e_stats viewed as an array, or nullptr
+  const float4* col_lut;      // per global column: x, y, phi, 0
+  const float* row_lut;       // per row: z
+  int* work;                  // [0] work-queue head, [1] deferred count
+  int* err;                   // error flags (ERR_*), latched until m3e_check
+  int* defer_list;            // frame ids for the CTA stage
+  int grab;                   // frames per work-queue grab
+  m3e_dump dump;              // all pointers null unless debugging
+};
+
+enum { ST_FRAMES = 0, ST_HITS, ST_PAIRS, ST_TTESTS, ST_TRIP, ST_TRK, ST_ETEST, ST_COMBO, ST_VTX, ST_DEFER,
+       ST_REASON0 };
+
+enum { ERR_BADHIT = 1, ERR_NEGSIZE = 2 };
+
+// Host-side launchers (m3e_kernels.cu).
+cudaError_t launch_select(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
+cudaError_t launch_deferred(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
+cudaError_t launch_plain(const DevCfg& c, const KParams& p, bool debug, cudaStream_t s);
+int select_blocks_per_sm();
+size_t select_smem_bytes();
+size_t cta_smem_bytes();
+
+}  // namespace m3e

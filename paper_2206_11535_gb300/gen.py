@@ -244,10 +244,18 @@ def _gen_chunk(geo, rng, f0, nf, n_tracks, signal_mask, noise_mean, ms, digitise
     return fr[order], ad[order], tr[order], ly[order], pos[order], tracks
 
 
+def _chunk_job(job):
+    """One independently seeded chunk of frames (a process-pool task)."""
+    cfg, seed, c0, nf, counts, fsig, lam, ms, digitise, noise, p_range, cos_range = job
+    rng = np.random.default_rng([seed, 1 + c0 // CHUNK_FRAMES])
+    return _gen_chunk(Geometry(cfg), rng, c0, nf, counts, fsig, lam, ms, digitise, noise, p_range, cos_range)
+
+
 def generate(n_frames: int, mean_tracks=10.0, noise_per_layer=0.5, signal_every: int | None = 10,
              seed: int = 1, ms: bool = True, digitise: bool = True, noise: bool = True,
              track_counts: np.ndarray | None = None, noise_scale: np.ndarray | None = None,
-             p_range=(15.0, 53.0), cos_range=(-0.8, 0.8), cfg: dict | None = None) -> dict:
+             p_range=(15.0, 53.0), cos_range=(-0.8, 0.8), cfg: dict | None = None,
+             workers: int | None = None) -> dict:
     """Draw ``n_frames`` frames.
 
     mean_tracks      Poisson mean of background tracks per frame (ignored if track_counts given)
@@ -256,6 +264,8 @@ def generate(n_frames: int, mean_tracks=10.0, noise_per_layer=0.5, signal_every:
     ms / digitise / noise  switch multiple scattering, pixel digitisation, noise off
     track_counts     explicit background tracks per frame (lognormal mixes and the like)
     noise_scale      per-frame multiplier of noise_per_layer
+    workers          processes for chunks of 65,536 frames (spawned; the output does
+                     not depend on it)
     Returns dict with ``hits`` (int32), ``off`` (int64, F+1), per-hit truth ``hit_track``
     (global track id or -1), ``hit_layer``, ``hit_pos`` (float64 true crossing points of
     track hits, pixel centres of noise hits), per-track truth ``trk_*`` and
@@ -274,12 +284,25 @@ def generate(n_frames: int, mean_tracks=10.0, noise_per_layer=0.5, signal_every:
     frames, addrs, trks, lays, poss = [], [], [], [], []
     tr_all = {}
     base_track = 0
+    jobs = []
     for c0 in range(0, n_frames, CHUNK_FRAMES):
         nf = min(CHUNK_FRAMES, n_frames - c0)
-        rng = np.random.default_rng([seed, 1 + c0 // CHUNK_FRAMES])
         lam = noise_per_layer if noise_scale is None else noise_per_layer * np.asarray(noise_scale[c0:c0 + nf], float)
-        fr, ad, tr, ly, pos, tracks = _gen_chunk(geo, rng, c0, nf, track_counts[c0:c0 + nf], fsig[c0:c0 + nf],
-                                                 lam, ms, digitise, noise, p_range, cos_range)
+        jobs.append((cfg, seed, c0, nf, track_counts[c0:c0 + nf], fsig[c0:c0 + nf], lam, ms, digitise, noise,
+                     p_range, cos_range))
+    if workers is None:
+        import sys
+        main_file = getattr(sys.modules.get("__main__"), "__file__", None)
+        spawnable = main_file is None or os.path.exists(main_file)  # spawn re-imports the main script
+        workers = min(len(jobs), os.cpu_count() or 1, 16) if spawnable and len(jobs) >= 4 else 1
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            results = list(ex.map(_chunk_job, jobs))
+    else:
+        results = [_chunk_job(j) for j in jobs]
+    for fr, ad, tr, ly, pos, tracks in results:
         tr = np.where(tr >= 0, tr + base_track, -1)
         base_track += tracks["frame"].size
         frames.append(fr); addrs.append(ad); trks.append(tr); lays.append(ly); poss.append(pos)

@@ -1,0 +1,248 @@
+"""Python binding of libm3e (``include/m3e.h``): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts torch
+tensors (device memory, streams) and numpy arrays (host memory) into the plain
+pointers and sizes of the C ABI.  Importing it loads ``libm3e.so`` and raises if
+the library has not been built (``paper_2206_11535_gb300.build.build()``):
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libm3e.so")
+
+OK, EINVAL, ENOMEM, EBADHIT, ECUDA, EBUSY, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+DROP, VERTEX, TRIPLET_OVERFLOW, TRACK_OVERFLOW, COMBO_OVERFLOW, HIT_OVERFLOW, ERR_BADHIT = range(7)
+REASONS = ("DROP", "VERTEX", "TRIPLET_OVERFLOW", "TRACK_OVERFLOW", "COMBO_OVERFLOW", "HIT_OVERFLOW", "ERR_BADHIT")
+
+
+class M3EError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"m3e error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("size", C.c_uint32),
+                ("r_mm", C.c_double * 4), ("half_len_mm", C.c_double * 4),
+                ("n_ladders", C.c_int32 * 4), ("n_cols", C.c_int32 * 4), ("n_rows", C.c_int32 * 4),
+                ("pitch_mm", C.c_double), ("B_T", C.c_double), ("field_scale", C.c_double),
+                ("x_over_X0", C.c_double * 4),
+                ("k_MeV_per_T_mm", C.c_double), ("m_mu_MeV", C.c_double), ("m_e_MeV", C.c_double),
+                ("target_r_mm", C.c_double), ("target_half_len_mm", C.c_double),
+                ("dlambda_max", C.c_double), ("phi01_max", C.c_double), ("phi12_max", C.c_double),
+                ("rtc_min", C.c_double), ("rtc_max", C.c_double), ("chi2_track_max", C.c_double),
+                ("e_window", C.c_double), ("isect_margin", C.c_double), ("vtx_chi2_max", C.c_double),
+                ("target_dist_max", C.c_double), ("ptot_max", C.c_double),
+                ("max_hits", C.c_int32), ("max_triplets", C.c_int32), ("max_tracks", C.c_int32),
+                ("max_combos", C.c_int32)]
+
+
+STATS_FIELDS = ("frames", "hits", "pair_tests", "triplet_tests", "triplets", "tracks", "energy_tests", "combos",
+                "vertexed", "deferred")
+N_STATS = len(STATS_FIELDS) + 8
+
+
+class Dump(C.Structure):
+    _fields_ = [("cap_trip", C.c_int32), ("cap_combo", C.c_int32),
+                ("n_trip", C.c_void_p), ("trip", C.c_void_p), ("trk_status", C.c_void_p), ("trk_val", C.c_void_p),
+                ("n_combo", C.c_void_p), ("combo", C.c_void_p), ("combo_val", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2206_11535_gb300.build.build() "
+                           "(the selection has no CPU path)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64 = C.c_void_p, C.c_int64
+    lib.m3e_create.argtypes = [C.POINTER(Config), C.c_int, C.POINTER(vp)]
+    lib.m3e_destroy.argtypes = [vp]
+    for name in ("m3e_select_frames", "m3e_select_frames_plain"):
+        getattr(lib, name).argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.m3e_select_frames_debug.argtypes = [vp, vp, vp, i64, vp, vp, C.POINTER(Dump), vp]
+    lib.m3e_select_frames_host.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    lib.m3e_check.argtypes = [vp, vp]
+    lib.m3e_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    lib.m3e_last_launch_count.argtypes = [vp]
+    lib.m3e_last_error_string.restype = C.c_char_p
+    lib.m3e_set_profiling.argtypes = [vp, C.c_int]
+    lib.m3e_kernel_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    return lib
+
+
+lib = _load()
+
+
+def version() -> int:
+    return lib.m3e_version()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise M3EError(rc, lib.m3e_last_error_string().decode())
+
+
+def config_from_json(cfg: dict, **override) -> Config:
+    """Fill the library's parameter struct from the JSON parameter dictionary."""
+    g, cu, ca = cfg["geometry"], cfg["cuts"], cfg["caps"]
+    c = Config()
+    c.size = C.sizeof(Config)
+    c.r_mm[:] = g["r_mm"]; c.half_len_mm[:] = g["half_len_mm"]
+    c.n_ladders[:] = g["n_ladders"]; c.n_cols[:] = g["n_cols"]; c.n_rows[:] = g["n_rows"]
+    c.pitch_mm = g["pitch_mm"]
+    c.B_T = cfg["field"]["B_T"]; c.field_scale = cfg["field"]["field_scale"]
+    c.x_over_X0[:] = cfg["material"]["x_over_X0"]
+    k = cfg["constants"]
+    c.k_MeV_per_T_mm = k["k_MeV_per_T_mm"]; c.m_mu_MeV = k["m_mu_MeV"]; c.m_e_MeV = k["m_e_MeV"]
+    c.target_r_mm = cfg["target"]["r_mm"]; c.target_half_len_mm = cfg["target"]["half_len_mm"]
+    for name in ("dlambda_max", "phi01_max", "phi12_max", "rtc_min", "rtc_max", "chi2_track_max", "e_window",
+                 "isect_margin", "vtx_chi2_max", "target_dist_max", "ptot_max"):
+        setattr(c, name, float(cu[name]))
+    for name in ("max_hits", "max_triplets", "max_tracks", "max_combos"):
+        setattr(c, name, int(ca[name]))
+    for kk, v in override.items():
+        setattr(c, kk, v)
+    return c
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Context:
+    """An m3e context on one CUDA device (``m3e_create`` / ``m3e_destroy``)."""
+
+    def __init__(self, cfg: dict | Config | None = None, device: int = 0):
+        if cfg is None:
+            from . import gen
+            cfg = gen.load_config()
+        self.config = cfg if isinstance(cfg, Config) else config_from_json(cfg)
+        self.device = device
+        h = C.c_void_p()
+        _check(lib.m3e_create(C.byref(self.config), device, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib.m3e_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- entry points (device tensors) -------------------------------------------------------
+    def _outs(self, hits, off, keep, reason):
+        import torch
+        nf = off.numel() - 1
+        dev = off.device
+        if keep is None:
+            keep = torch.empty(nf, dtype=torch.uint8, device=dev)
+        if reason is None:
+            reason = torch.empty(nf, dtype=torch.uint8, device=dev)
+        return nf, keep, reason
+
+    def select_frames(self, hits, off, keep=None, reason=None, stats=None, stream=None):
+        """``m3e_select_frames`` on int32 ``hits`` and int64 ``off`` (CUDA tensors).
+        Returns (keep, reason) uint8 tensors."""
+        nf, keep, reason = self._outs(hits, off, keep, reason)
+        _check(lib.m3e_select_frames(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason), _ptr(stats),
+                                     _stream(stream)))
+        return keep, reason
+
+    def select_frames_plain(self, hits, off, keep=None, reason=None, stats=None, stream=None):
+        """``m3e_select_frames_plain``: one CTA per frame, one launch per batch."""
+        nf, keep, reason = self._outs(hits, off, keep, reason)
+        _check(lib.m3e_select_frames_plain(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
+                                           _ptr(stats), _stream(stream)))
+        return keep, reason
+
+    def select_frames_debug(self, hits, off, cap_trip=768, cap_combo=1024, stream=None):
+        """``m3e_select_frames_debug``: returns keep, reason and the candidate record
+        (torch tensors on the device, frame-major)."""
+        import torch
+        nf, keep, reason = self._outs(hits, off, None, None)
+        dev = off.device
+        rec = dict(n_trip=torch.zeros(nf, dtype=torch.int32, device=dev),
+                   trip=torch.full((nf, cap_trip, 4), -2, dtype=torch.int32, device=dev),
+                   trk_status=torch.full((nf, cap_trip), -1, dtype=torch.int32, device=dev),
+                   trk_val=torch.zeros((nf, cap_trip, 4), dtype=torch.float32, device=dev),
+                   n_combo=torch.zeros(nf, dtype=torch.int32, device=dev),
+                   combo=torch.full((nf, cap_combo, 4), -2, dtype=torch.int32, device=dev),
+                   combo_val=torch.zeros((nf, cap_combo, 4), dtype=torch.float32, device=dev))
+        d = Dump(cap_trip, cap_combo, *[_ptr(rec[k]) for k in ("n_trip", "trip", "trk_status", "trk_val", "n_combo",
+                                                                  "combo", "combo_val")])
+        _check(lib.m3e_select_frames_debug(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
+                                           C.byref(d), _stream(stream)))
+        rec["keep"], rec["reason"] = keep, reason
+        return rec
+
+    def select_frames_host(self, hits: np.ndarray, off: np.ndarray, keep=None, reason=None, stream=None):
+        """``m3e_select_frames_host`` on host arrays (numpy or pinned torch CPU tensors).
+        Synchronise ``stream`` before reading keep/reason."""
+        nf = (off.numel() if hasattr(off, "numel") else off.size) - 1
+        if keep is None:
+            keep = np.empty(nf, np.uint8)
+        if reason is None:
+            reason = np.empty(nf, np.uint8)
+        _check(lib.m3e_select_frames_host(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
+                                          _stream(stream)))
+        return keep, reason
+
+    def check(self, stream=None) -> int:
+        """``m3e_check``: synchronise the stream; raises M3EError(EBADHIT) when a frame
+        held an invalid address since the last check."""
+        _check(lib.m3e_check(self._h, _stream(stream)))
+        return OK
+
+    def set_launch(self, frames_per_grab: int, ctas_per_sm: int = 0):
+        _check(lib.m3e_set_launch(self._h, frames_per_grab, ctas_per_sm))
+
+    def last_launch_count(self) -> int:
+        return lib.m3e_last_launch_count(self._h)
+
+    def set_profiling(self, on: bool = True):
+        _check(lib.m3e_set_profiling(self._h, int(on)))
+
+    def kernel_times(self) -> tuple[float, float]:
+        """(main kernel ms, deferred-frame kernel ms) of the last timed select call."""
+        a, b = C.c_float(), C.c_float()
+        _check(lib.m3e_kernel_times(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+
+def stats_dict(t) -> dict:
+    """Decode an ``m3e_stats`` buffer (int64 tensor of N_STATS entries)."""
+    v = [int(x) for x in t.cpu().tolist()]
+    d = dict(zip(STATS_FIELDS, v[:len(STATS_FIELDS)]))
+    d["reasons"] = v[len(STATS_FIELDS):len(STATS_FIELDS) + 8]
+    return d
+
+
+def new_stats(device="cuda"):
+    import torch
+    return torch.zeros(N_STATS, dtype=torch.int64, device=device)

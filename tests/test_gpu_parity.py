@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the GPU."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2206_11535_gb300 import gen
+
+from . import parity as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def m3e():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_11535_gb300 import m3e as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(m3e, cfg):
+    c = m3e.Context(cfg, 0)
+    yield c
+    c.close()
+
+
+def _dev(d):
+    return torch.from_numpy(d["hits"]).cuda(), torch.from_numpy(d["off"]).cuda()
+
+
+def _np(rec):
+    return {k: v.cpu().numpy() for k, v in rec.items()}
+
+
+def _check_results(res, max_boundary_frac=0.01):
+    s = P.summary(res)
+    fails = [r for r in res if r.status == "fail"]
+    msg = "\n".join(f"frame {r.frame}: {r.fails[:4]}" for r in fails[:10])
+    assert s["fail"] == 0, f"{s}\n{msg}"
+    assert s["boundary"] <= max_boundary_frac * len(res) + 1, s
+    return s
+
+
+def test_c1_parity_all_frames(ctx, ocfg):
+    """1,000 frames of the parity workload: every candidate list and decision."""
+    d = gen.workload("c1")
+    hits, off = _dev(d)
+    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024))
+    s = _check_results(P.compare_batch(ocfg, d["hits"], d["off"], rec))
+    print("c1 parity", s)
+    keep, reason = ctx.select_frames(hits, off)
+    assert (reason.cpu().numpy() == rec["reason"]).all()
+    assert (keep.cpu().numpy() == rec["keep"]).all()
+    keep_p, reason_p = ctx.select_frames_plain(hits, off)
+    assert (reason_p.cpu().numpy() == rec["reason"]).all()
+    ctx.check()
+
+
+def test_c2_sample_parity(ctx, ocfg):
+    """2,000 frames of the throughput workload's generator (seed 2)."""
+    d = gen.workload("c2", n_frames=2000)
+    hits, off = _dev(d)
+    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024))
+    s = _check_results(P.compare_batch(ocfg, d["hits"], d["off"], rec))
+    print("c2 sample parity", s)
+
+
+def test_c2_full_size_sampled(ctx, ocfg):
+    """The full 1,000,000-frame throughput batch, in the launch configuration the
+    benchmark times; 400 sampled frames checked against the oracle one by one,
+    plus invariants over all frames."""
+    d = gen.workload("c2")
+    hits, off = _dev(d)
+    keep, reason = ctx.select_frames(hits, off)
+    ctx.check()
+    r = reason.cpu().numpy()
+    k = keep.cpu().numpy()
+    assert ((k == 1) == (r != 0)).all()
+    assert r.max() <= 6
+    rng = np.random.default_rng(123)
+    sample = np.sort(rng.choice(d["off"].size - 1, 400, replace=False))
+    diff = []
+    for f in sample:
+        o = O.select_frame(ocfg, d["hits"][d["off"][f]:d["off"][f + 1]], records=False)
+        if o["reason"] != r[f]:
+            diff.append(int(f))
+    # any disagreement must be a boundary frame of the candidate-level comparison
+    for f in diff:
+        sub = gen_subbatch(d, [f])
+        rec = _np(ctx.select_frames_debug(*_dev(sub), cap_trip=1024, cap_combo=1024))
+        res = P.compare_frame(ocfg, sub["hits"], P.record_of_frame(rec, 0), f)
+        assert res.status == "boundary", (f, res.fails)
+    assert len(diff) <= 4
+
+
+def gen_subbatch(d, frames):
+    parts = [d["hits"][d["off"][f]:d["off"][f + 1]] for f in frames]
+    off = np.zeros(len(frames) + 1, np.int64)
+    off[1:] = np.cumsum([p.size for p in parts])
+    return dict(hits=np.concatenate(parts) if parts else np.zeros(0, np.int32), off=off)
+
+
+def test_permutation_invariance(ctx):
+    d = gen.workload("c1", n_frames=300, seed=9)
+    rng = np.random.default_rng(1)
+    hp = d["hits"].copy()
+    for f in range(300):
+        a, b = d["off"][f], d["off"][f + 1]
+        hp[a:b] = hp[a:b][rng.permutation(b - a)]
+    r1 = _np(ctx.select_frames_debug(*_dev(d)))
+    r2 = _np(ctx.select_frames_debug(torch.from_numpy(hp).cuda(), torch.from_numpy(d["off"]).cuda()))
+    assert (r1["reason"] == r2["reason"]).all()
+    assert (r1["n_trip"] == r2["n_trip"]).all() and (r1["n_combo"] == r2["n_combo"]).all()
+    for f in range(0, 300, 7):
+        a = d["off"][f]
+        n = min(r1["n_trip"][f], 768)
+        s1 = sorted(tuple(d["hits"][a + r1["trip"][f, t, :3]]) for t in range(n))
+        s2 = sorted(tuple(hp[a + r2["trip"][f, t, :3]]) for t in range(n))
+        assert s1 == s2
+
+
+def test_edge_cases(ctx, m3e, cfg, ocfg):
+    g = cfg["geometry"]
+    frames = []
+    frames.append(np.zeros(0, np.int32))                                               # empty frame
+    frames.append(gen.encode([0, 1, 2], [0, 0, 0], [1, 1, 1], [5, 5, 5]))              # no layer 3
+    frames.append(gen.encode([0, 1, 0, 1], [0, 0, 1, 1], [3, 3, 5, 5], [100, 100, 200, 200]))  # two layers
+    base = gen.generate(3, 10.0, 0.5, None, seed=5)
+    f0 = base["hits"][base["off"][0]:base["off"][1]]
+    frames.append(np.concatenate([f0, f0]))                                            # duplicated hits
+    heavy = gen.generate(2, 80.0, 5.0, None, seed=6)                                   # deferred to the CTA stage
+    frames.append(heavy["hits"][heavy["off"][0]:heavy["off"][1]])
+    frames.append(heavy["hits"][heavy["off"][1]:heavy["off"][2]])
+    big = gen.generate(1, 1500.0, 0.0, None, seed=7)                                   # more than max_hits
+    frames.append(big["hits"])
+    frames.append(f0)                                                                  # ordinary frame last
+    off = np.zeros(len(frames) + 1, np.int64)
+    off[1:] = np.cumsum([f.size for f in frames])
+    hits = np.concatenate(frames).astype(np.int32)
+    d = dict(hits=hits, off=off)
+    assert frames[4].size > 160 and big["hits"].size > cfg["caps"]["max_hits"]
+    rec = _np(ctx.select_frames_debug(*_dev(d), cap_trip=1024, cap_combo=1024))
+    res = P.compare_batch(ocfg, hits, off, rec)
+    _check_results(res, max_boundary_frac=0.5)
+    assert rec["reason"][0] == 0 and rec["reason"][1] == 0 and rec["reason"][2] == 0
+    assert rec["reason"][6] == m3e.HIT_OVERFLOW
+    keep, reason = ctx.select_frames(*_dev(d))
+    assert (reason.cpu().numpy() == rec["reason"]).all()
+    ctx.check()
+    # an invalid address: frame kept with ERR_BADHIT, EBADHIT latched until checked
+    bad = np.concatenate([f0, gen.encode([2], [g["n_ladders"][2]], [0], [0])]).astype(np.int32)
+    d2 = gen_subbatch(dict(hits=np.concatenate([f0, bad]), off=np.array([0, f0.size, f0.size + bad.size])), [0, 1])
+    keep, reason = ctx.select_frames(*_dev(d2))
+    assert reason.cpu().tolist()[1] == m3e.ERR_BADHIT and keep.cpu().tolist()[1] == 1
+    with pytest.raises(m3e.M3EError) as e:
+        ctx.check()
+    assert e.value.code == m3e.EBADHIT
+    ctx.check()  # cleared
+    # zero frames
+    z = dict(hits=np.zeros(0, np.int32), off=np.zeros(1, np.int64))
+    keep, reason = ctx.select_frames(*_dev(z))
+    assert keep.numel() == 0
+
+
+def test_small_caps_overflow_parity(m3e, cfg):
+    """Caps lowered so that every overflow path triggers: decisions equal the
+    oracle's under the same caps."""
+    over = dict(max_triplets=12, max_tracks=6, max_combos=4)
+    import copy
+    c2 = copy.deepcopy(cfg)
+    c2["caps"].update(over)
+    oc = O.make_config(c2)
+    d = gen.workload("c1", n_frames=400, seed=19)
+    with m3e.Context(c2, 0) as ctx:
+        rec = _np(ctx.select_frames_debug(*_dev(d), cap_trip=64, cap_combo=64))
+    res = P.compare_batch(oc, d["hits"], d["off"], rec)
+    _check_results(res)
+    counts = np.bincount(rec["reason"], minlength=7)
+    assert counts[2] > 0 and counts[3] > 0 and counts[4] > 0, counts
+
+
+def test_host_entry_matches_device(ctx):
+    d = gen.workload("c2", n_frames=50000, seed=12)
+    keep, reason = ctx.select_frames(*_dev(d))
+    hh = torch.from_numpy(d["hits"]).pin_memory()
+    ho = torch.from_numpy(d["off"]).pin_memory()
+    hk = torch.empty(d["off"].size - 1, dtype=torch.uint8).pin_memory()
+    hr = torch.empty(d["off"].size - 1, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.current_stream()
+    ctx.select_frames_host(hh, ho, hk, hr, stream=s)
+    s.synchronize()
+    assert (hr.numpy() == reason.cpu().numpy()).all()
+    assert (hk.numpy() == keep.cpu().numpy()).all()
+
+
+def test_stats_counters(ctx, m3e, ocfg):
+    d = gen.workload("c1", n_frames=500, seed=13)
+    st = m3e.new_stats()
+    keep, reason = ctx.select_frames(*_dev(d), stats=st)
+    torch.cuda.synchronize()
+    s = m3e.stats_dict(st)
+    assert sum(s["reasons"]) == 500
+    assert s["frames"] == 500 - s["reasons"][5] - s["reasons"][6]
+    assert s["hits"] <= d["hits"].size
+    _, _, cnt = O.select_frames(ocfg, d["hits"], d["off"], 4, counts=True)
+    assert abs(s["triplets"] - cnt[:, 3].sum()) <= 5
+    assert abs(s["tracks"] - cnt[:, 4].sum()) <= 5
