@@ -33,8 +33,15 @@ WORKLOAD = ("full-rate throughput: 1,000,000 frames per GPU, Poisson(20) tracks/
             "|cos theta| < 0.8, double-cone target), 2 noise hits/layer, signal decay in 0.1% of frames, "
             "4 layers r=25/31/73/85 mm, B=1 T, 80 um pixels, int32 addresses")
 # Arithmetic operations per work item of the method's formulas (FMA = 2, each
-# transcendental, division or square root = 1); see DESIGN.md "Roofline".
-OPS_PER_ITEM = {"pair_tests": 4, "triplet_tests": 6, "triplets": 460, "energy_tests": 7, "vertexed": 640}
+# transcendental, division or square root = 1), grouped by the stage kernel that
+# does the work; see DESIGN.md "Roofline".
+STAGE_OPS = {
+    "stage1 decode+sort+cuts": {"pair_tests": 4, "triplet_tests": 6},
+    "stage2 track fits": {"triplets": 460},
+    "stage3 energy test": {"energy_tests": 7},
+    "stage4 vertex": {"combos": 75, "vertexed": 565},
+    "stage5 decision": {},
+}
 
 
 def parse():
@@ -107,15 +114,15 @@ class Clocks:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("m3e_kernels.cu", "m3e_internal.cuh"):
+    for f in ("m3e_staged.cu", "m3e_device.cuh", "m3e_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2206_11535_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(n_frames: int):
-    """DRAM bytes per launch of the persistent kernel from the committed ncu summary,
+    """DRAM bytes of one staged batch (all stage kernels) from the committed ncu summary,
     scaled to n_frames; None when the summary was taken on other kernel sources."""
-    p = os.path.join(ROOT, "profiles", "select_warp_c2_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "staged_c2_traffic.txt")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -234,7 +241,7 @@ def main():
         for _ in range(steps):
             fn()
             if profile:
-                ks.append(ctx.kernel_times())
+                ks.append(ctx.stage_times())
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
@@ -244,17 +251,17 @@ def main():
             ms = float(t.item())
         return ms, ks
 
-    # main arm: persistent kernel, kernel durations recorded on the launching stream
+    # main arm: the staged form, kernel durations recorded on the launching stream
     ctx.set_profiling(True)
     with Clocks(local) as clk:
         ms, ks = timed(lambda: ctx.select_frames(hits, off, keep, reason, stream=stream), args.steps,
                        args.warmup, profile=True)
     launches = ctx.last_launch_count() * args.steps
     ctx.set_profiling(False)
-    # plain per-frame form, same batch
-    ms_plain, _ = timed(lambda: ctx.select_frames_plain(hits, off, keep, reason, stream=stream),
-                        max(2, args.steps // 2), 1)
-    plain_steps = max(2, args.steps // 2)
+    # the fused (one persistent kernel, warp per frame) and plain (CTA per frame) forms
+    alt_steps = max(2, args.steps // 2)
+    ms_fused, _ = timed(lambda: ctx.select_frames_fused(hits, off, keep, reason, stream=stream), alt_steps, 1)
+    ms_plain, _ = timed(lambda: ctx.select_frames_plain(hits, off, keep, reason, stream=stream), alt_steps, 1)
     # end to end from pinned host memory through the C ABI host entry point
     e2e = None
     if not args.no_e2e:
@@ -266,35 +273,44 @@ def main():
         e2e = {"value": world * nf * args.steps / (ms_e2e / 1e3), "unit": "frames/s",
                "h2d_bytes_per_step": int(hh.numel() * 4 + ho.numel() * 8), "d2h_bytes_per_step": int(2 * nf),
                "ms_per_step": ms_e2e / args.steps}
+    # the main arm's decisions are those of the last timed staged call
+    ctx.select_frames(hits, off, keep, reason, stream=stream)
     ctx.check()
 
     value = world * nf * args.steps / (ms / 1e3)
-    kmain = float(np.mean([k[0] for k in ks])) if ks else float("nan")
-    kdef = float(np.mean([k[1] for k in ks])) if ks else float("nan")
+    st_ms = np.mean(np.array(ks), axis=0) if ks else np.full(6, np.nan)
     props = torch.cuda.get_device_properties(dev)
     cl = clk.summary()
     f_mhz = cl["sm_mhz"] or 1455.0
-    ops = sum(stats[k] * v for k, v in OPS_PER_ITEM.items())
-    achieved = ops / (kmain / 1e3) / 1e12
     peak = props.multi_processor_count * 128 * 2 * f_mhz * 1e6 / 1e12
+    stages = []
+    for i, (name, per) in enumerate(STAGE_OPS.items()):
+        ops = sum(stats[k] * v for k, v in per.items())
+        t = float(st_ms[i])
+        stages.append({"kernel": name, "ms": t, "ops": ops, "tflops": ops / (t / 1e3) / 1e12 if t > 0 else 0.0,
+                       "frac_of_peak": ops / (t / 1e3) / 1e12 / peak if t > 0 else 0.0})
+    stages.append({"kernel": "deferred frames (CTA per frame)", "ms": float(st_ms[5])})
+    dom = max(stages[:5], key=lambda x: x["ms"])
     tr = recorded_traffic(nf)
-    roof = {"bound": "alu", "kernel": "k_select_warp (persistent warp-per-frame selection)",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": tr, "kernel_ms": kmain, "deferred_kernel_ms": kdef,
-            "ops_per_launch": ops, "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf,
-            "hbm_gbs_at_kernel_time": (nh * 4 + (nf + 1) * 8 + 2 * nf) / (kmain / 1e3) / 1e9,
+    roof = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
+            "frac": dom["frac_of_peak"], "traffic": tr, "kernel_ms": dom["ms"],
             "peak_source": f"FP32 lanes x 2 x SM clock: {props.multi_processor_count} SMs x 128 x 2 x "
-                           f"{f_mhz:.0f} MHz (median sampled under load)"}
+                           f"{f_mhz:.0f} MHz (median sampled under load)",
+            "stages": stages,
+            "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf}
     out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "frames_per_gpu": nf, "hits_per_gpu": nh,
-                      "l2": "inputs larger than L2 (no flush)", "form": "persistent warp-per-frame, device queue",
+                      "l2": "inputs larger than L2 (no flush)",
+                      "form": "staged: 5 persistent kernels regrouping the batch by candidate",
                       "parallelism": f"{world} independent GPU shard(s), no collective on the data path"},
            "hits_per_s": world * nh * args.steps / (ms / 1e3),
-           "plain_per_frame": {"value": world * nf * plain_steps / (ms_plain / 1e3), "unit": "frames/s",
-                               "ms_per_step": ms_plain / plain_steps,
-                               "speedup_of_persistent": (ms_plain / plain_steps) / (ms / args.steps)},
+           "fused_form": {"value": world * nf * alt_steps / (ms_fused / 1e3), "unit": "frames/s",
+                          "ms_per_step": ms_fused / alt_steps},
+           "plain_per_frame": {"value": world * nf * alt_steps / (ms_plain / 1e3), "unit": "frames/s",
+                               "ms_per_step": ms_plain / alt_steps,
+                               "speedup_of_staged": (ms_plain / alt_steps) / (ms / args.steps)},
            "kept_fraction": float(keep.float().mean().item()),
            "reasons": dict(zip(m3e.REASONS, stats["reasons"][:7])),
            "roofline": roof, "e2e": e2e, "clocks": cl, "gpu_launches": launches}

@@ -115,7 +115,8 @@ typedef struct {
   int32_t cap_trip;        /* records kept per frame for triplets (<= max_triplets) */
   int32_t cap_combo;       /* records kept per frame for combinations (<= max_combos) */
   int32_t* n_trip;         /* [F] selected triplets (full count) */
-  int32_t* trip;           /* [F][cap_trip][4] i0, i1, i2, i3 (i3 = -1 when no 4th hit) */
+  int32_t* trip;           /* [F][cap_trip][4] i0, i1, i2, i3 (i3 = -1 when no 4th hit; among
+                              hits with equal address, which one is reported is unspecified) */
   int32_t* trk_status;     /* [F][cap_trip] 0 fit1 invalid, 1 no layer-3 crossing, 2 no layer-3
                               hit, 3 fit2 invalid, 4 chi2 >= cut, 5 kept */
   float* trk_val;          /* [F][cap_trip][4] kappa_bar, theta01, chi2, 4th-hit metric */
@@ -135,22 +136,32 @@ int m3e_create(const m3e_config* cfg, int cuda_device, m3e_ctx** out);
 /* Release the context and its device memory (synchronises the context's device). */
 int m3e_destroy(m3e_ctx* ctx);
 
-/* Select frames (the whole method of the paper, every step in CUDA kernels):
- * persistent warp-per-frame kernel over a device work queue, frames too large
- * for a warp's shared-memory stage re-run by a CTA-per-frame kernel.
- * d_stats may be NULL.  n_frames may be 0. */
+/* Select frames (the whole method of the paper, every step in CUDA kernels),
+ * the throughput form: five persistent kernels that regroup the batch by
+ * candidate (frames -> selected triplets -> tracks -> combinations -> decisions,
+ * the candidates in device scratch); frames larger than a stage's capacity are
+ * re-run by a CTA-per-frame kernel with identical decisions.  d_stats may be
+ * NULL.  n_frames may be 0. */
 int m3e_select_frames(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
                       uint8_t* d_keep, uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t stream);
+
+/* The same decisions through the fused form: one persistent kernel in which a
+ * warp runs every stage of a frame in shared memory, frames from a device work
+ * queue (lowest latency per frame; the form the streaming path uses). */
+int m3e_select_frames_fused(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                            uint8_t* d_keep, uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t stream);
 
 /* The same decisions through the plain per-frame form: one CTA per frame, one
  * launch per batch (the layout of the paper's main kernel, Algorithm 1). */
 int m3e_select_frames_plain(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
                             uint8_t* d_keep, uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t stream);
 
-/* m3e_select_frames with the candidate record filled in; the vertex stage then
- * evaluates every combination instead of stopping at the first passing one. */
-int m3e_select_frames_debug(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
-                            uint8_t* d_keep, uint8_t* d_reason, const m3e_dump* dump, cudaStream_t stream);
+/* A selection with the candidate record filled in, through form 0 (staged, as
+ * m3e_select_frames), 1 (fused) or 2 (plain); the vertex stage then evaluates
+ * every combination instead of stopping at the first passing one. */
+int m3e_select_frames_debug(m3e_ctx* ctx, int form, const int32_t* d_hits, const int64_t* d_frame_off,
+                            int64_t n_frames, uint8_t* d_keep, uint8_t* d_reason, const m3e_dump* dump,
+                            cudaStream_t stream);
 
 /* End to end from HOST memory: copies the hits and offsets to the device in
  * chunks, selects, and copies keep/reason back, overlapping the copies of one
@@ -171,13 +182,16 @@ int m3e_set_launch(m3e_ctx* ctx, int frames_per_grab, int ctas_per_sm);
 /* Number of kernel launches the last select call enqueued. */
 int m3e_last_launch_count(const m3e_ctx* ctx);
 
-/* Kernel timing.  With on = 1, each m3e_select_frames / _plain call records CUDA
- * events on the caller's stream around each of its kernels.  m3e_kernel_times
- * waits for the events of the last call and returns the duration in ms of the
- * main kernel (persistent warp kernel, or the plain CTA kernel) and of the
- * deferred-frame kernel (0 for the plain form).  Timing adds no device sync. */
+/* Kernel timing.  With on = 1, each m3e_select_frames / _fused / _plain call
+ * records CUDA events on the caller's stream around its kernels.
+ * m3e_kernel_times waits for the events of the last call and returns the
+ * duration in ms of the main kernels (the five staged kernels, the fused kernel
+ * or the plain kernel) and of the deferred-frame kernel (0 for the plain form).
+ * m3e_stage_times returns up to 6 durations of the last staged call: stages 1-5
+ * and the deferred-frame kernel.  Timing adds no device sync. */
 int m3e_set_profiling(m3e_ctx* ctx, int on);
 int m3e_kernel_times(m3e_ctx* ctx, float* main_ms, float* deferred_ms);
+int m3e_stage_times(m3e_ctx* ctx, float* ms, int n);
 
 const char* m3e_last_error_string(void);
 int m3e_version(void);

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libm3e.so")
-UNITS = ["m3e_kernels.cu", "m3e_abi.cu"]
+UNITS = ["m3e_staged.cu", "m3e_fused.cu", "m3e_abi.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "--prec-div=true", "--prec-sqrt=true", "-ftz=false", "--fmad=true",
@@ -29,13 +29,15 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    hdrs = [os.path.join(SRC, "m3e_internal.cuh"), os.path.join(ROOT, "include", "m3e.h"), __file__]
+def build(force: bool = False, verbose: bool = False, src_dir: str = SRC, out: str = OUT) -> str:
+    """Compile the units of ``src_dir`` and link ``out`` (defaults: this package)."""
+    hdrs = [os.path.join(src_dir, "m3e_internal.cuh"), os.path.join(src_dir, "m3e_device.cuh"),
+            os.path.join(ROOT, "include", "m3e.h"), __file__]
     objs = []
     jobs = []
     for u in UNITS:
-        src = os.path.join(SRC, u)
-        obj = os.path.join(SRC, u.replace(".cu", ".o"))
+        src = os.path.join(src_dir, u)
+        obj = os.path.join(src_dir, u.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
             jobs.append([NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj])
@@ -45,10 +47,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
             if verbose:
                 sys.stderr.write(r.stderr)
-    if force or jobs or _stale(OUT, objs):
+    if force or jobs or _stale(out, objs):
         subprocess.check_call([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-cudart", "static",
-                               "-o", OUT] + objs)
-    return OUT
+                               "-o", out] + objs)
+    return out
 
 
 if __name__ == "__main__":

@@ -47,34 +47,56 @@ constexpr int HOST_CHUNKS = 8;  // chunks of the host entry point (double-buffer
 
 }  // namespace
 
+// Device scratch of one launch sequence: work queue, deferred-frame list and the
+// global candidate arrays of the staged form.  The context holds one set for the
+// device entry points and two for the double-buffered host entry point.
+struct Scratch {
+  int* work = nullptr;                      // [0] work-queue head, [1] deferred count
+  unsigned long long* counters = nullptr;   // staged: [0] triplets, [1] combinations, [2] stage-3 queue
+  int* defer = nullptr;
+  int64_t defer_cap = 0;
+  float* hf = nullptr;                      // hx, hy, hz, hphi
+  uint32_t* haddr = nullptr;
+  uint16_t* hidx = nullptr;
+  int64_t hits_cap = 0;
+  uint16_t* l3 = nullptr;
+  int* fint = nullptr;                      // fstate, ftbase, fntrip, ffound, fncombo
+  long long* fcbase = nullptr;
+  int64_t frames_cap = 0;
+  int4* trip = nullptr;
+  uint8_t* tstatus = nullptr;
+  float4* trec = nullptr;
+  int64_t trip_cap = 0;
+  int4* combo = nullptr;
+  int64_t combo_cap = 0;
+};
+
 struct m3e_ctx {
   int device = 0;
   int sms = 1;
-  int blocks_per_sm = 1;
+  int fused_bpsm = 1, s1_bpsm = 1, s2_bpsm = 1, s3_bpsm = 1, s4_bpsm = 1;
   int grab = 4;
   m3e_config cfg{};
   DevCfg dc{};
   float4* col_lut = nullptr;
   float* row_lut = nullptr;
-  int* work = nullptr;          // [0] queue head, [1] deferred count, [2] error flags
-  int* defer_list = nullptr;
-  int64_t defer_cap = 0;
+  int* err = nullptr;           // latched error flags
   int* h_err = nullptr;         // pinned error-flag readback
   int last_launches = 0;
+  Scratch main;
   // host entry point staging
+  Scratch hsc[2];
   cudaStream_t hs[2] = {nullptr, nullptr};
   cudaEvent_t he[2] = {nullptr, nullptr};
   int32_t* d_hits[2] = {nullptr, nullptr};
   int64_t* d_off[2] = {nullptr, nullptr};
   uint8_t* d_out[2] = {nullptr, nullptr};
-  int* d_work2[2] = {nullptr, nullptr};
-  int* d_defer2[2] = {nullptr, nullptr};
   int64_t cap_hits[2] = {0, 0}, cap_frames[2] = {0, 0};
   // kernel timing
   bool prof = false;
   bool prof_valid = false;
-  bool prof_plain = false;
-  cudaEvent_t pe[3] = {nullptr, nullptr, nullptr};
+  int prof_kind = 0;            // 0 staged, 1 fused, 2 plain
+  cudaEvent_t pe[8] = {};
 };
 
 namespace {
@@ -150,6 +172,7 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
   d.kB = (float)(c.k_MeV_per_T_mm * c.B_T * c.field_scale);
   d.chi2_trk = (float)c.chi2_track_max;
   d.r3 = (float)c.r_mm[3];
+  d.colw3 = (float)(TWO_PI / d.ntot[3] + 1e-4);
   d.me2 = (float)(c.m_e_MeV * c.m_e_MeV);
   d.m_mu = (float)c.m_mu_MeV;
   d.e_win = (float)c.e_window;
@@ -166,28 +189,114 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
   d.max_combo = c.max_combos;
 }
 
-KParams base_params(m3e_ctx* x) {
+KParams base_params(m3e_ctx* x, Scratch& sc) {
   KParams p{};
   p.col_lut = x->col_lut;
   p.row_lut = x->row_lut;
-  p.work = x->work;
-  p.err = x->work + 2;
-  p.defer_list = x->defer_list;
+  p.work = sc.work;
+  p.err = x->err;
+  p.defer_list = sc.defer;
   p.grab = x->grab;
   return p;
 }
 
-int ensure_defer(m3e_ctx* x, int64_t n) {
-  if (n <= x->defer_cap) return M3E_OK;
-  int64_t cap = x->defer_cap ? x->defer_cap : 4096;
-  while (cap < n) cap *= 2;
-  if (x->defer_list) CUDA_TRY(cudaFree(x->defer_list));
-  x->defer_list = nullptr;
-  x->defer_cap = 0;
-  if (cudaMalloc(&x->defer_list, sizeof(int) * cap) != cudaSuccess)
-    return fail(M3E_ENOMEM, "deferred list of %lld frames", (long long)cap);
-  x->defer_cap = cap;
+template <class T>
+int grow(T*& ptr, int64_t& cap, int64_t need, size_t elem, const char* what) {
+  if (need <= cap) return M3E_OK;
+  if (ptr) CUDA_TRY(cudaFree(ptr));
+  ptr = nullptr;
+  cap = 0;
+  if (cudaMalloc(&ptr, elem * (size_t)need) != cudaSuccess) return fail(M3E_ENOMEM, "%s: %lld entries", what, (long long)need);
+  cap = need;
   return M3E_OK;
+}
+
+// Scratch for a batch of nf frames (staged arrays only when staged: each pending
+// frame keeps its sorted hits in a fixed slot of S1_HITS entries).
+int ensure_scratch(Scratch& sc, int64_t nf, bool staged) {
+  const int64_t nh = nf * S1_HITS;
+  int64_t one = sc.work ? 1 : 0;
+  int rc = grow(sc.work, one, 1, 4 * sizeof(int), "work counters");
+  if (rc) return rc;
+  int64_t one2 = sc.counters ? 1 : 0;
+  rc = grow(sc.counters, one2, 1, 4 * sizeof(unsigned long long), "counters");
+  if (rc) return rc;
+  rc = grow(sc.defer, sc.defer_cap, nf > 4096 ? nf : 4096, sizeof(int), "deferred list");
+  if (rc || !staged) return rc;
+  int64_t hc = sc.hits_cap;
+  if (nh > hc) {
+    int64_t c0 = hc, c1 = hc, c2 = hc;
+    rc = grow(sc.hf, c0, nh, 4 * sizeof(float), "sorted hits");
+    if (!rc) rc = grow(sc.haddr, c1, nh, sizeof(uint32_t), "sorted addresses");
+    if (!rc) rc = grow(sc.hidx, c2, nh, sizeof(uint16_t), "sorted input indices");
+    if (rc) return rc;
+    sc.hits_cap = nh;
+  }
+  if (nf > sc.frames_cap) {
+    int64_t c0 = sc.frames_cap, c1 = sc.frames_cap, c2 = sc.frames_cap;
+    rc = grow(sc.l3, c0, nf, (NB + 1) * sizeof(uint16_t), "layer-3 bins");
+    if (!rc) rc = grow(sc.fint, c1, nf, 5 * sizeof(int), "frame state");
+    if (!rc) rc = grow(sc.fcbase, c2, nf, sizeof(long long), "frame combination base");
+    if (rc) return rc;
+    sc.frames_cap = nf;
+  }
+  const int64_t lim = ((int64_t)1 << 31) - (1 << 16);
+  int64_t tc = 64 * nf > (1 << 16) ? 64 * nf : (1 << 16);
+  tc = tc < lim ? tc : lim;
+  if (tc > sc.trip_cap) {
+    int64_t c0 = sc.trip_cap, c1 = sc.trip_cap, c2 = sc.trip_cap;
+    rc = grow(sc.trip, c0, tc, sizeof(int4), "triplets");
+    if (!rc) rc = grow(sc.tstatus, c1, tc, 1, "track status");
+    if (!rc) rc = grow(sc.trec, c2, tc, 4 * sizeof(float4), "track records");
+    if (rc) return rc;
+    sc.trip_cap = tc;
+  }
+  int64_t cc = 192 * nf > (1 << 16) ? 192 * nf : (1 << 16);
+  cc = cc < lim ? cc : lim;
+  return grow(sc.combo, sc.combo_cap, cc, sizeof(int4), "combinations");
+}
+
+void free_scratch(Scratch& sc) {
+  cudaFree(sc.work);
+  cudaFree(sc.counters);
+  cudaFree(sc.defer);
+  cudaFree(sc.hf);
+  cudaFree(sc.haddr);
+  cudaFree(sc.hidx);
+  cudaFree(sc.l3);
+  cudaFree(sc.fint);
+  cudaFree(sc.fcbase);
+  cudaFree(sc.trip);
+  cudaFree(sc.tstatus);
+  cudaFree(sc.trec);
+  cudaFree(sc.combo);
+  sc = Scratch();
+}
+
+SParams staged_params(const Scratch& sc) {
+  SParams s{};
+  const int64_t H = sc.hits_cap, F = sc.frames_cap;
+  s.hx = sc.hf;
+  s.hy = sc.hf + H;
+  s.hz = sc.hf + 2 * H;
+  s.hphi = sc.hf + 3 * H;
+  s.haddr = sc.haddr;
+  s.hidx = sc.hidx;
+  s.l3 = sc.l3;
+  s.fstate = sc.fint;
+  s.ftbase = sc.fint + F;
+  s.fntrip = sc.fint + 2 * F;
+  s.ffound = sc.fint + 3 * F;
+  s.fncombo = sc.fint + 4 * F;
+  s.fcbase = sc.fcbase;
+  s.trip = sc.trip;
+  s.tstatus = sc.tstatus;
+  s.trec = sc.trec;
+  s.combo = sc.combo;
+  s.counters = sc.counters;
+  s.trip_cap = sc.trip_cap;
+  s.combo_cap = sc.combo_cap;
+  return s;
 }
 
 int check_batch(const int32_t* hits, const int64_t* off, int64_t n, const uint8_t* keep, const uint8_t* reason) {
@@ -197,17 +306,35 @@ int check_batch(const int32_t* hits, const int64_t* off, int64_t n, const uint8_
   return M3E_OK;
 }
 
-// Enqueue the persistent kernel and the deferred-frame kernel on stream s with
-// the given work/deferred scratch.
-int enqueue_select(m3e_ctx* x, KParams p, bool debug, cudaStream_t s, bool timed) {
-  CUDA_TRY(cudaMemsetAsync(p.work, 0, 2 * sizeof(int), s));
-  const int grid = x->sms * x->blocks_per_sm;
-  if (timed) CUDA_TRY(cudaEventRecord(x->pe[0], s));
-  CUDA_TRY(launch_select(x->dc, p, grid, debug, s));
-  if (timed) CUDA_TRY(cudaEventRecord(x->pe[1], s));
+enum { FORM_STAGED = 0, FORM_FUSED = 1, FORM_PLAIN = 2 };
+
+// Enqueue one batch on stream s: form 0 staged (5 kernels), 1 fused warp kernel,
+// 2 plain CTA-per-frame kernel; forms 0 and 1 finish with the deferred-frame
+// kernel.  Timing events are recorded when `timed`.
+int enqueue(m3e_ctx* x, Scratch& sc, KParams p, int form, bool debug, cudaStream_t s, bool timed) {
+  if (form == FORM_PLAIN) {
+    if (timed) CUDA_TRY(cudaEventRecord(x->pe[0], s));
+    CUDA_TRY(launch_plain(x->dc, p, debug, s));
+    if (timed) CUDA_TRY(cudaEventRecord(x->pe[1], s));
+    x->last_launches = 1;
+    return M3E_OK;
+  }
+  CUDA_TRY(cudaMemsetAsync(sc.work, 0, 2 * sizeof(int), s));
+  if (form == FORM_FUSED) {
+    if (timed) CUDA_TRY(cudaEventRecord(x->pe[0], s));
+    CUDA_TRY(launch_fused(x->dc, p, x->sms * x->fused_bpsm, debug, s));
+    if (timed) CUDA_TRY(cudaEventRecord(x->pe[1], s));
+    CUDA_TRY(launch_deferred(x->dc, p, 2 * x->sms, debug, s));
+    if (timed) CUDA_TRY(cudaEventRecord(x->pe[2], s));
+    x->last_launches = 2;
+    return M3E_OK;
+  }
+  CUDA_TRY(cudaMemsetAsync(sc.counters, 0, 3 * sizeof(unsigned long long), s));
+  const int grids[4] = {x->sms * x->s1_bpsm, x->sms * x->s2_bpsm, x->sms * x->s3_bpsm, x->sms * x->s4_bpsm};
+  CUDA_TRY(launch_staged(x->dc, p, staged_params(sc), grids, debug, s, timed ? x->pe : nullptr));
   CUDA_TRY(launch_deferred(x->dc, p, 2 * x->sms, debug, s));
-  if (timed) CUDA_TRY(cudaEventRecord(x->pe[2], s));
-  x->last_launches = 2;
+  if (timed) CUDA_TRY(cudaEventRecord(x->pe[6], s));
+  x->last_launches = 6;
   return M3E_OK;
 }
 
@@ -239,7 +366,11 @@ int m3e_create(const m3e_config* cfg, int cuda_device, m3e_ctx** out) {
     return fail(M3E_ECUDA, "cudaGetDeviceProperties");
   }
   x->sms = prop.multiProcessorCount;
-  x->blocks_per_sm = select_blocks_per_sm();
+  x->fused_bpsm = fused_blocks_per_sm();
+  x->s1_bpsm = stage_blocks_per_sm(1);
+  x->s2_bpsm = stage_blocks_per_sm(2);
+  x->s3_bpsm = stage_blocks_per_sm(3);
+  x->s4_bpsm = stage_blocks_per_sm(4);
   // look-up tables in FP64, rounded once
   int ncolt = 0, nrowt = 0;
   for (int L = 0; L < 4; ++L) {
@@ -260,13 +391,12 @@ int m3e_create(const m3e_config* cfg, int cuda_device, m3e_ctx** out) {
   }
   bool ok = cudaMalloc(&x->col_lut, sizeof(float4) * ncolt) == cudaSuccess &&
             cudaMalloc(&x->row_lut, sizeof(float) * nrowt) == cudaSuccess &&
-            cudaMalloc(&x->work, 4 * sizeof(int)) == cudaSuccess &&
-            cudaMallocHost(&x->h_err, sizeof(int)) == cudaSuccess;
+            cudaMalloc(&x->err, sizeof(int)) == cudaSuccess && cudaMallocHost(&x->h_err, sizeof(int)) == cudaSuccess;
   if (ok)
     ok = cudaMemcpy(x->col_lut, cl.data(), sizeof(float4) * ncolt, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(x->row_lut, rl.data(), sizeof(float) * nrowt, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemset(x->work, 0, 4 * sizeof(int)) == cudaSuccess;
-  if (ok) ok = ensure_defer(x, 1 << 16) == M3E_OK;
+         cudaMemset(x->err, 0, sizeof(int)) == cudaSuccess;
+  if (ok) ok = ensure_scratch(x->main, 1 << 12, false) == M3E_OK;
   if (!ok) {
     m3e_destroy(x);
     return fail(M3E_ENOMEM, "device allocation in m3e_create");
@@ -281,19 +411,18 @@ int m3e_destroy(m3e_ctx* x) {
   cudaDeviceSynchronize();
   cudaFree(x->col_lut);
   cudaFree(x->row_lut);
-  cudaFree(x->work);
-  cudaFree(x->defer_list);
+  cudaFree(x->err);
   if (x->h_err) cudaFreeHost(x->h_err);
+  free_scratch(x->main);
   for (int i = 0; i < 2; ++i) {
+    free_scratch(x->hsc[i]);
     cudaFree(x->d_hits[i]);
     cudaFree(x->d_off[i]);
     cudaFree(x->d_out[i]);
-    cudaFree(x->d_work2[i]);
-    cudaFree(x->d_defer2[i]);
     if (x->hs[i]) cudaStreamDestroy(x->hs[i]);
     if (x->he[i]) cudaEventDestroy(x->he[i]);
   }
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 8; ++i)
     if (x->pe[i]) cudaEventDestroy(x->pe[i]);
   delete x;
   return M3E_OK;
@@ -303,10 +432,10 @@ int m3e_set_launch(m3e_ctx* x, int frames_per_grab, int ctas_per_sm) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
   if (frames_per_grab < 1 || frames_per_grab > 64) return fail(M3E_EINVAL, "frames_per_grab 1..64");
   DeviceGuard guard(x->device);
-  const int maxb = select_blocks_per_sm();
+  const int maxb = fused_blocks_per_sm();
   if (ctas_per_sm < 0 || ctas_per_sm > maxb) return fail(M3E_EINVAL, "ctas_per_sm 0..%d", maxb);
   x->grab = frames_per_grab;
-  x->blocks_per_sm = ctas_per_sm ? ctas_per_sm : maxb;
+  x->fused_bpsm = ctas_per_sm ? ctas_per_sm : maxb;
   return M3E_OK;
 }
 
@@ -315,7 +444,7 @@ int m3e_last_launch_count(const m3e_ctx* x) { return x ? x->last_launches : 0; }
 int m3e_set_profiling(m3e_ctx* x, int on) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
   DeviceGuard guard(x->device);
-  for (int i = 0; i < 3 && on; ++i)
+  for (int i = 0; i < 8 && on; ++i)
     if (!x->pe[i]) CUDA_TRY(cudaEventCreate(&x->pe[i]));
   x->prof = on != 0;
   x->prof_valid = false;
@@ -326,22 +455,37 @@ int m3e_kernel_times(m3e_ctx* x, float* main_ms, float* deferred_ms) {
   if (!x || !main_ms || !deferred_ms) return fail(M3E_EINVAL, "NULL argument");
   if (!x->prof_valid) return fail(M3E_ESTATE, "no timed select call since profiling was enabled");
   DeviceGuard guard(x->device);
-  CUDA_TRY(cudaEventSynchronize(x->pe[x->prof_plain ? 1 : 2]));
-  CUDA_TRY(cudaEventElapsedTime(main_ms, x->pe[0], x->pe[1]));
+  const int last = x->prof_kind == FORM_STAGED ? 6 : (x->prof_kind == FORM_FUSED ? 2 : 1);
+  const int mid = x->prof_kind == FORM_STAGED ? 5 : 1;
+  CUDA_TRY(cudaEventSynchronize(x->pe[last]));
+  CUDA_TRY(cudaEventElapsedTime(main_ms, x->pe[0], x->pe[mid]));
   *deferred_ms = 0.f;
-  if (!x->prof_plain) CUDA_TRY(cudaEventElapsedTime(deferred_ms, x->pe[1], x->pe[2]));
+  if (last != mid) CUDA_TRY(cudaEventElapsedTime(deferred_ms, x->pe[mid], x->pe[last]));
+  return M3E_OK;
+}
+
+int m3e_stage_times(m3e_ctx* x, float* ms, int n) {
+  if (!x || !ms || n < 1) return fail(M3E_EINVAL, "bad argument");
+  if (!x->prof_valid || x->prof_kind != FORM_STAGED) return fail(M3E_ESTATE, "no timed staged select call");
+  DeviceGuard guard(x->device);
+  CUDA_TRY(cudaEventSynchronize(x->pe[6]));
+  for (int i = 0; i < n && i < 6; ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], x->pe[i], x->pe[i + 1]));
   return M3E_OK;
 }
 
 static int select_common(m3e_ctx* x, const int32_t* hits, const int64_t* off, int64_t n, uint8_t* keep,
-                         uint8_t* reason, m3e_stats* stats, const m3e_dump* dump, bool plain, cudaStream_t s) {
+                         uint8_t* reason, m3e_stats* stats, const m3e_dump* dump, int form, cudaStream_t s) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
   int rc = check_batch(hits, off, n, keep, reason);
   if (rc) return rc;
+  if (form < FORM_STAGED || form > FORM_PLAIN) return fail(M3E_EINVAL, "form must be 0, 1 or 2");
   x->last_launches = 0;
+  x->prof_valid = false;
   if (n == 0) return M3E_OK;
   DeviceGuard guard(x->device);
-  KParams p = base_params(x);
+  rc = ensure_scratch(x->main, n, form == FORM_STAGED);
+  if (rc) return rc;
+  KParams p = base_params(x, x->main);
   p.hits = hits;
   p.off = off;
   p.n_frames = n;
@@ -357,49 +501,41 @@ static int select_common(m3e_ctx* x, const int32_t* hits, const int64_t* off, in
     p.dump = *dump;
   }
   const bool timed = x->prof && dump == nullptr;
-  x->prof_valid = false;
-  if (plain) {
-    if (timed) CUDA_TRY(cudaEventRecord(x->pe[0], s));
-    CUDA_TRY(launch_plain(x->dc, p, dump != nullptr, s));
-    if (timed) CUDA_TRY(cudaEventRecord(x->pe[1], s));
-    x->last_launches = 1;
-    x->prof_valid = timed;
-    x->prof_plain = true;
-    return M3E_OK;
-  }
-  rc = ensure_defer(x, n);
-  if (rc) return rc;
-  p.defer_list = x->defer_list;
-  rc = enqueue_select(x, p, dump != nullptr, s, timed);
+  rc = enqueue(x, x->main, p, form, dump != nullptr, s, timed);
   x->prof_valid = timed && rc == M3E_OK;
-  x->prof_plain = false;
+  x->prof_kind = form;
   return rc;
 }
 
 int m3e_select_frames(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n, uint8_t* d_keep,
                       uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t s) {
-  return select_common(x, d_hits, d_off, n, d_keep, d_reason, d_stats, nullptr, false, s);
+  return select_common(x, d_hits, d_off, n, d_keep, d_reason, d_stats, nullptr, FORM_STAGED, s);
+}
+
+int m3e_select_frames_fused(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n, uint8_t* d_keep,
+                            uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t s) {
+  return select_common(x, d_hits, d_off, n, d_keep, d_reason, d_stats, nullptr, FORM_FUSED, s);
 }
 
 int m3e_select_frames_plain(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n, uint8_t* d_keep,
                             uint8_t* d_reason, m3e_stats* d_stats, cudaStream_t s) {
-  return select_common(x, d_hits, d_off, n, d_keep, d_reason, d_stats, nullptr, true, s);
+  return select_common(x, d_hits, d_off, n, d_keep, d_reason, d_stats, nullptr, FORM_PLAIN, s);
 }
 
-int m3e_select_frames_debug(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n, uint8_t* d_keep,
-                            uint8_t* d_reason, const m3e_dump* dump, cudaStream_t s) {
+int m3e_select_frames_debug(m3e_ctx* x, int form, const int32_t* d_hits, const int64_t* d_off, int64_t n,
+                            uint8_t* d_keep, uint8_t* d_reason, const m3e_dump* dump, cudaStream_t s) {
   if (!dump) return fail(M3E_EINVAL, "dump is NULL");
-  return select_common(x, d_hits, d_off, n, d_keep, d_reason, nullptr, dump, false, s);
+  return select_common(x, d_hits, d_off, n, d_keep, d_reason, nullptr, dump, form, s);
 }
 
 int m3e_check(m3e_ctx* x, cudaStream_t s) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
   DeviceGuard guard(x->device);
-  CUDA_TRY(cudaMemcpyAsync(x->h_err, x->work + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(x->h_err, x->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   const int e = *x->h_err;
   if (e) {
-    CUDA_TRY(cudaMemsetAsync(x->work + 2, 0, sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(x->err, 0, sizeof(int), s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return fail(M3E_EBADHIT, "invalid pixel address or frame size seen (flags %d)", e);
   }
@@ -408,13 +544,14 @@ int m3e_check(m3e_ctx* x, cudaStream_t s) {
 
 // End to end from host memory.  Frames are cut into chunks of about equal hit
 // count; chunk k uses buffer set k % 2 and internal stream k % 2, so the copies
-// of one chunk overlap the kernels of the other.
+// of one chunk overlap the kernels of the other.  Each chunk runs the staged form.
 int m3e_select_frames_host(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_off, int64_t n, uint8_t* h_keep,
                            uint8_t* h_reason, cudaStream_t s) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
   int rc = check_batch(h_hits, h_off, n, h_keep, h_reason);
   if (rc) return rc;
   x->last_launches = 0;
+  x->prof_valid = false;
   if (n == 0) return M3E_OK;
   if (h_off[n] < h_off[0]) return fail(M3E_EINVAL, "frame_off must be non-decreasing");
   if (h_off[n] > h_off[0] && !h_hits) return fail(M3E_EINVAL, "hits is NULL");
@@ -444,44 +581,32 @@ int m3e_select_frames_host(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_o
     const int b = k & 1;
     const int64_t nf = f1 - f0, nh = h_off[f1] - h_off[f0];
     cudaStream_t hs = x->hs[b];
-    if (nh > x->cap_hits[b]) {
-      if (x->d_hits[b]) CUDA_TRY(cudaFree(x->d_hits[b]));
-      x->d_hits[b] = nullptr;
-      x->cap_hits[b] = 0;
-      const int64_t cap = nh + nh / 4 + 1024;
-      if (cudaMalloc(&x->d_hits[b], sizeof(int32_t) * cap) != cudaSuccess) return fail(M3E_ENOMEM, "staging hits");
-      x->cap_hits[b] = cap;
-    }
-    if (nf > x->cap_frames[b]) {
+    rc = grow(x->d_hits[b], x->cap_hits[b], nh + nh / 4 + 1024, sizeof(int32_t), "staging hits");
+    if (rc) return rc;
+    if (nf + 1 > x->cap_frames[b]) {
       cudaFree(x->d_off[b]);
       cudaFree(x->d_out[b]);
-      cudaFree(x->d_work2[b]);
-      cudaFree(x->d_defer2[b]);
       x->d_off[b] = nullptr;
       x->d_out[b] = nullptr;
-      x->d_work2[b] = nullptr;
-      x->d_defer2[b] = nullptr;
       x->cap_frames[b] = 0;
       const int64_t cap = nf + nf / 4 + 1024;
       if (cudaMalloc(&x->d_off[b], sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
-          cudaMalloc(&x->d_out[b], 2 * cap) != cudaSuccess || cudaMalloc(&x->d_work2[b], 4 * sizeof(int)) != cudaSuccess ||
-          cudaMalloc(&x->d_defer2[b], sizeof(int) * cap) != cudaSuccess)
+          cudaMalloc(&x->d_out[b], 2 * cap) != cudaSuccess)
         return fail(M3E_ENOMEM, "staging frames");
-      CUDA_TRY(cudaMemsetAsync(x->d_work2[b], 0, 4 * sizeof(int), hs));
       x->cap_frames[b] = cap;
     }
+    rc = ensure_scratch(x->hsc[b], nf, true);
+    if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(x->d_hits[b], h_hits + h_off[f0], sizeof(int32_t) * nh, cudaMemcpyHostToDevice, hs));
     CUDA_TRY(cudaMemcpyAsync(x->d_off[b], h_off + f0, sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice, hs));
-    KParams p = base_params(x);
+    KParams p = base_params(x, x->hsc[b]);
     p.hits = x->d_hits[b];
     p.off = x->d_off[b];
     p.off_base = h_off[f0];
     p.n_frames = nf;
     p.keep = x->d_out[b];
     p.reason = x->d_out[b] + x->cap_frames[b];
-    p.work = x->d_work2[b];
-    p.defer_list = x->d_defer2[b];
-    rc = enqueue_select(x, p, false, hs, false);
+    rc = enqueue(x, x->hsc[b], p, FORM_STAGED, false, hs, false);
     if (rc) return rc;
     launches += x->last_launches;
     CUDA_TRY(cudaMemcpyAsync(h_keep + f0, p.keep, nf, cudaMemcpyDeviceToHost, hs));

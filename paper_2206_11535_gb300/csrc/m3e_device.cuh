@@ -1,19 +1,8 @@
-// Selection kernels of libm3e: the whole per-frame method of the paper
-// (Algorithm 1: load, selection cuts, track reconstruction, vertex fit, store)
-// in FP32 with IEEE division and square root.
-//
-// One routine, process_frame<Group>, runs a frame on a group of threads: a warp
-// (persistent kernel, warp per frame, frames from a device work queue) or a
-// whole CTA (frames too large for a warp's shared-memory stage, and the plain
-// per-frame form).  Per frame:
-//   A  decode the int32 pixel addresses and histogram them by (layer, phi bin)
-//   B  counting sort into shared memory: x, y, z, phi from FP64-built tables
-//   C  selection cuts: for each layer-1 hit, layer-0 and layer-2 partners from
-//      the phi bins that can pass the Phi cuts, then Delta lambda and r_tc
-//   D  triplet fit, layer-3 extrapolation and closest hit, second triplet fit,
-//      global curvature and chi2 cut (one thread per selected triplet)
-//   E  energy test of every e+ e+ e- combination
-//   F  vertex of each surviving combination, early exit once one passes
+// Device code shared by the fused and the staged selection kernels: thread
+// groups, the shared-memory frame stage, decode, the triplet fit, track
+// reconstruction and the vertex, all in FP32 with IEEE division and square root.
+#pragma once
+
 #include <cfloat>
 
 #include "m3e_internal.cuh"
@@ -46,15 +35,18 @@ struct CtaGroup {
 
 // ------------------------------------------------------------------ shared-memory stage
 
-struct TrkS {          // a kept track, as the vertex stage needs it
-  float cx, cy, rt;    // transverse circle through the layer-0 and layer-1 hits
-  float R, ct, st;     // 3D radius and cos/sin of the first segment's polar angle
-  float p, E, sms;     // momentum, energy, MS width at layer 0
-  float h0x, h0y, h0z; // layer-0 hit
-  float ah0;           // angle of the layer-0 hit seen from the circle centre
-  float eps;           // turning sense, +1 clockwise (positive charge)
-  int tid;             // index of the triplet it came from
-  int pad;
+// Kept tracks as structure of arrays: the energy test reads E[] with one index for
+// all lanes (broadcast) and the vertex stage gathers by track index without the
+// bank conflicts of a 64-byte record stride.
+template <int CK>
+struct TrkSoA {
+  float cx[CK], cy[CK], rt[CK];     // transverse circle through the layer-0 and layer-1 hits
+  float R[CK], ct[CK], st[CK];      // 3D radius and cos/sin of the first segment's polar angle
+  float p[CK], E[CK], sms[CK];      // momentum, energy, MS width at layer 0
+  float h0x[CK], h0y[CK], h0z[CK];  // layer-0 hit
+  float ah0[CK];                    // angle of the layer-0 hit seen from the circle centre
+  float eps[CK];                    // turning sense, +1 clockwise (positive charge)
+  int tid[CK];                      // index of the triplet it came from
 };
 
 template <int CH, int CT, int CK, int CC>
@@ -65,7 +57,7 @@ struct FrameSm {
   uint8_t bin[CH];
   uint16_t bstart[NBK + 1];
   int bcur[NBK];
-  TrkS trk[CK];                 // positives from the front, negatives from the back
+  TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
     ushort4 trip[CT];           // selected triplets (sorted-hit indices)
     uint32_t combo[CC];         // e+ e+ e- combinations (track indices), after the fits
@@ -108,62 +100,68 @@ __device__ __forceinline__ float wrap_pi(float a) {  // (-2 pi, 2 pi) -> [-pi, p
   return a;
 }
 
-// sin(x) - x cos(x) for x in (0, pi].  For small x the two terms cancel to
-// x^3/3, so the Taylor series sum_k (-1)^(k+1) 2k x^(2k+1) / (2k+1)! is used
-// below 0.5 (five terms: truncation below FP32 rounding).
-__device__ __forceinline__ float sin_minus_xcos(float x) {
+// sin(x) - x cos(x) for x in (0, pi], given s = sin x and c = cos x.  For small x
+// the two terms cancel to x^3/3, so the Taylor series
+// sum_k (-1)^(k+1) 2k x^(2k+1) / (2k+1)! is used below 0.5 (five terms:
+// truncation below FP32 rounding).
+__device__ __forceinline__ float sin_minus_xcos(float x, float s, float c) {
   if (x < 0.5f) {
     const float x2 = x * x;
-    float s = 1.f / 3991680.f;
-    s = s * x2 - 1.f / 45360.f;
-    s = s * x2 + 1.f / 840.f;
-    s = s * x2 - 1.f / 30.f;
-    s = s * x2 + 1.f / 3.f;
-    return s * x2 * x;
+    float t = 1.f / 3991680.f;
+    t = t * x2 - 1.f / 45360.f;
+    t = t * x2 + 1.f / 840.f;
+    t = t * x2 - 1.f / 30.f;
+    t = t * x2 + 1.f / 3.f;
+    return t * x2 * x;
   }
-  float sx, cx;
-  sincosf(x, &sx, &cx);
-  return sx - x * cx;
+  return s - x * c;
 }
 
 // ------------------------------------------------------------------ triplet fit
 
 struct SegF {
-  float phi, RC, th, dphi, dth;
+  float phi, RC, th, dphi, dth, zp;
 };
 
 // One segment of the circle solution: chord d, axial length z, transverse radius
 // Rct of the circle through the triplet.  Helix relations d = 2 R_t sin(Phi/2),
 // z = R_t Phi cot(theta), R_t = R sin(theta) give the 3D radius R_C, the polar
 // angle theta_C and the derivatives dPhi/dR, dtheta/dR at the circle solution.
+// sin(Phi/2) = d / 2R_t on either arc (the long arc turns by 2 pi minus the short
+// one, which leaves the sine of the half angle and flips its cosine).
 __device__ __forceinline__ SegF segment(float d, float z, float Rct, bool obtuse) {
   SegF s;
-  float ph = 2.f * asinf(fminf(1.f, d / (2.f * Rct)));
-  if (obtuse) ph = TWO_PI_F - ph;
+  const float sh = fminf(1.f, d / (2.f * Rct));
+  float ph = 2.f * asinf(sh);
+  float ch = sqrtf(fmaxf((1.f - sh) * (1.f + sh), 0.f));
+  if (obtuse) {
+    ph = TWO_PI_F - ph;
+    ch = -ch;
+  }
   const float zp = z / ph;
   s.RC = sqrtf(Rct * Rct + zp * zp);
   s.th = atan2f(Rct * ph, z);
-  float sh, ch;
-  sincosf(0.5f * ph, &sh, &ch);
   const float sh2 = sh * sh;
   const float dRdphi = -(d * d * ch / (8.f * sh2 * sh) + zp * zp / ph) / s.RC;
   s.dphi = 1.f / dRdphi;
   const float g = ph / (2.f * sh);
-  const float gp = sin_minus_xcos(0.5f * ph) / (2.f * sh2);
+  const float gp = sin_minus_xcos(0.5f * ph, sh, ch) / (2.f * sh2);
   const float dg = d * g;
   s.dth = z * d * gp / (z * z + dg * dg) * s.dphi;
   s.phi = ph;
+  s.zp = zp;
   return s;
 }
 
 struct TFitF {
-  bool valid;
   float eps, Rct, ccx, ccy;
   float Rref;                  // expansion point of the kink model: R_C of segment 0
   float alpha, a0p, beta, b0p; // Phi_MS ~ alpha u + a0p, Theta_MS ~ beta u + b0p, u = R - Rref
   float s2;                    // sin^2 of the mean polar angle
   float kappa, skappa;
-  float thC0, thC1, RC0, dth0;
+  float thC0, RC0, dth0;
+  float zp1;                   // z / Phi of segment 1 = R_t cot(theta_C1)
+  int valid;
 };
 
 // Single triplet fit, hits a -> b -> c, scattering at b (Sec. "Single Triplet
@@ -171,11 +169,12 @@ struct TFitF {
 // minimum in the 3D radius.  The model is written in u = R - R_C0 so that the
 // small offsets (R_C0 - R_C1, theta_C1 - theta_C0) enter directly instead of as
 // differences of large products; the algebra equals the minimum of
-// [Phi_MS^2 sin^2(theta) + Theta_MS^2] / sigma_MS^2.
-__device__ __forceinline__ TFitF fit_triplet(float ax, float ay, float az, float bx, float by, float bz,
-                                             float cx, float cy, float cz, float hl, float kB) {
+// [Phi_MS^2 sin^2(theta) + Theta_MS^2] / sigma_MS^2.  Out of line: it runs twice
+// per track, and one copy keeps the kernel's instruction footprint small.
+__device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx, float by, float bz, float cx,
+                                          float cy, float cz, float hl, float kB) {
   TFitF f;
-  f.valid = false;
+  f.valid = 0;
   const float ux = ax - bx, uy = ay - by, vx = cx - bx, vy = cy - by;
   const float cross = ux * vy - uy * vx;
   const float u2 = ux * ux + uy * uy, v2 = vx * vx + vy * vy;
@@ -209,10 +208,10 @@ __device__ __forceinline__ TFitF fit_triplet(float ax, float ay, float az, float
   f.skappa = sms / sqrtf(den) / (Rs * Rs);
   if (!isfinite(f.kappa) || !isfinite(f.skappa) || !(f.skappa > 0.f)) return f;
   f.thC0 = s0.th;
-  f.thC1 = s1.th;
   f.RC0 = s0.RC;
   f.dth0 = s0.dth;
-  f.valid = true;
+  f.zp1 = s1.zp;
+  f.valid = 1;
   return f;
 }
 
@@ -221,6 +220,37 @@ __device__ __forceinline__ float kink_chi2(const TFitF& f, float R, float sg) {
   const float kp = f.alpha * u + f.a0p, kt = f.beta * u + f.b0p;
   return (kp * kp * f.s2 + kt * kt) / (sg * sg);
 }
+
+// ------------------------------------------------------------------ hit views
+
+// Hits of one frame, sorted by (layer, phi bin), as build_track reads them: from
+// the shared-memory stage of a fused kernel, or from global memory in the staged
+// form (pointers already offset to the frame).
+template <class S>
+struct SmHits {
+  const S& s;
+  __device__ __forceinline__ float x(int i) const { return s.x[i]; }
+  __device__ __forceinline__ float y(int i) const { return s.y[i]; }
+  __device__ __forceinline__ float z(int i) const { return s.z[i]; }
+  __device__ __forceinline__ float phi(int i) const { return s.phi[i]; }
+  __device__ __forceinline__ uint32_t addr(int i) const { return s.addr[i]; }
+  __device__ __forceinline__ int l3(int b) const { return s.bstart[3 * NB + b]; }  // layer-3 bin starts
+};
+
+struct GHits {
+  const float* __restrict__ xs;
+  const float* __restrict__ ys;
+  const float* __restrict__ zs;
+  const float* __restrict__ ps;
+  const uint32_t* __restrict__ as;
+  const uint16_t* __restrict__ l3s;  // NB + 1 layer-3 bin starts, frame-relative
+  __device__ __forceinline__ float x(int i) const { return __ldg(xs + i); }
+  __device__ __forceinline__ float y(int i) const { return __ldg(ys + i); }
+  __device__ __forceinline__ float z(int i) const { return __ldg(zs + i); }
+  __device__ __forceinline__ float phi(int i) const { return __ldg(ps + i); }
+  __device__ __forceinline__ uint32_t addr(int i) const { return __ldg(as + i); }
+  __device__ __forceinline__ int l3(int b) const { return __ldg(l3s + b); }
+};
 
 // ------------------------------------------------------------------ track reconstruction
 
@@ -233,16 +263,23 @@ struct TrackOut {
 // estimate the layer-3 point from the first triplet's circle and the second
 // segment's polar angle, take the closest layer-3 hit ((r3 dphi)^2 + dz^2, ties
 // to the smaller address), fit (h1, h2, h3), weighted mean curvature and chi2 of
-// both triplets at it, chi2 cut.  On success fills *t for the vertex stage.
-template <class S>
-__device__ TrackOut build_track(const S& sm, const DevCfg& C, int i0, int i1, int i2, TrkS* t) {
+// both triplets at it, chi2 cut.  A kept track is written to slot `slot` of the
+// track arrays by the caller (store_track).
+//
+// Closest hit: layer-3 hits are visited by phi bin in rings around the bin of the
+// estimated point.  Every hit of ring m >= 3 lies at least (m - 2) bin widths
+// minus one column from the estimated phi (one ring of slack covers a bin index
+// rounded across an edge), so once (r3 * that)^2 exceeds the best metric no
+// farther hit can win: the search returns the same hit as a scan of all hits.
+template <class V>
+__device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int i0, int i1, int i2, float* tr) {
   TrackOut o;
   o.status = 0;
   o.i3 = -1;
   o.kbar = o.th01 = o.chi2 = o.mbest = 0.f;
-  const float x0 = sm.x[i0], y0 = sm.y[i0], z0 = sm.z[i0];
-  const float x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
-  const float x2 = sm.x[i2], y2 = sm.y[i2], z2 = sm.z[i2];
+  const float x0 = v.x(i0), y0 = v.y(i0), z0 = v.z(i0);
+  const float x1 = v.x(i1), y1 = v.y(i1), z1 = v.z(i1);
+  const float x2 = v.x(i2), y2 = v.y(i2), z2 = v.z(i2);
   const TFitF f1 = fit_triplet(x0, y0, z0, x1, y1, z1, x2, y2, z2, C.hl[1], C.kB);
   if (!f1.valid) return o;
   const float r3 = C.r3;
@@ -254,37 +291,51 @@ __device__ TrackOut build_track(const S& sm, const DevCfg& C, int i0, int i1, in
   const float ux = f1.ccx / D, uy = f1.ccy / D;
   const float qx0 = a * ux - hh * uy, qy0 = a * uy + hh * ux;
   const float qx1 = a * ux + hh * uy, qy1 = a * uy - hh * ux;
-  const float a2 = atan2f(y2 - f1.ccy, x2 - f1.ccx);
-  const float al0 = wrap_2pi(f1.eps * (a2 - atan2f(qy0 - f1.ccy, qx0 - f1.ccx)));
-  const float al1 = wrap_2pi(f1.eps * (a2 - atan2f(qy1 - f1.ccy, qx1 - f1.ccx)));
+  // turning angle from h2 to each crossing q in the turning sense: the angle from
+  // (h2 - c) to (q - c) is atan2(cross, dot); clockwise turning decreases it
+  const float wx = x2 - f1.ccx, wy = y2 - f1.ccy;
+  const float vx0 = qx0 - f1.ccx, vy0 = qy0 - f1.ccy, vx1 = qx1 - f1.ccx, vy1 = qy1 - f1.ccy;
+  const float al0 = wrap_2pi(-f1.eps * atan2f(wx * vy0 - wy * vx0, wx * vx0 + wy * vy0));
+  const float al1 = wrap_2pi(-f1.eps * atan2f(wx * vy1 - wy * vx1, wx * vx1 + wy * vy1));
   const bool take1 = al1 < al0;
   const float al = take1 ? al1 : al0;
   const float qx = take1 ? qx1 : qx0, qy = take1 ? qy1 : qy0;
-  float s12, c12;
-  sincosf(f1.thC1, &s12, &c12);
-  const float z3 = z2 + f1.Rct * al * c12 / s12;
-  const float phi3 = atan2f(qy, qx);
+  const float z3 = z2 + al * f1.zp1;  // R_t * dPhi * cot(theta_C12)
+  float phi3 = atan2f(qy, qx);
+  if (phi3 < 0.f) phi3 += TWO_PI_F;
+  int b3 = (int)(phi3 * (NB / TWO_PI_F));
+  b3 = b3 < 0 ? 0 : (b3 >= NB ? NB - 1 : b3);
   int best = -1;
   float mb = FLT_MAX;
   uint32_t ab = 0;
-  const int l3a = sm.bstart[3 * NB], l3b = sm.bstart[4 * NB];
-  for (int j = l3a; j < l3b; ++j) {
-    const float dphi = wrap_pi(sm.phi[j] - phi3);
-    const float dz = sm.z[j] - z3;
-    const float m = (r3 * dphi) * (r3 * dphi) + dz * dz;
-    const uint32_t aj = sm.addr[j];
-    if (best < 0 || m < mb || (m == mb && aj < ab)) {
-      best = j;
-      mb = m;
-      ab = aj;
+  for (int m = 0; m <= NB / 2; ++m) {
+    if (m >= 3) {
+      const float dmin = (float)(m - 2) * (TWO_PI_F / NB) - C.colw3;
+      if (dmin > 0.f && (r3 * dmin) * (r3 * dmin) > mb) break;
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (side == 1 && (m == 0 || m == NB / 2)) continue;
+      const int bb = (b3 + (side ? -m : m)) & (NB - 1);
+      const int e = v.l3(bb + 1);
+      for (int j = v.l3(bb); j < e; ++j) {
+        const float dphi = wrap_pi(v.phi(j) - phi3);
+        const float dz = v.z(j) - z3;
+        const float mm = (r3 * dphi) * (r3 * dphi) + dz * dz;
+        const uint32_t aj = v.addr(j);
+        if (best < 0 || mm < mb || (mm == mb && aj < ab)) {
+          best = j;
+          mb = mm;
+          ab = aj;
+        }
+      }
     }
   }
   o.status = 2;
   if (best < 0) return o;
   o.i3 = best;
   o.mbest = mb;
-  const float x3 = sm.x[best], y3 = sm.y[best], z3h = sm.z[best];
-  const TFitF f2 = fit_triplet(x1, y1, z1, x2, y2, z2, x3, y3, z3h, C.hl[2], C.kB);
+  const TFitF f2 = fit_triplet(x1, y1, z1, x2, y2, z2, v.x(best), v.y(best), v.z(best), C.hl[2], C.kB);
   o.status = 3;
   if (!f2.valid) return o;
   const float w1 = 1.f / (f1.skappa * f1.skappa), w2 = 1.f / (f2.skappa * f2.skappa);
@@ -304,36 +355,85 @@ __device__ TrackOut build_track(const S& sm, const DevCfg& C, int i0, int i1, in
   // the layer-0 and layer-1 hits, centre on the side the track turns to
   float st, ct;
   sincosf(o.th01, &st, &ct);
-  t->R = Rb;
-  t->ct = ct;
-  t->st = st;
-  t->rt = Rb * st;
-  t->p = pb;
-  t->E = sqrtf(pb * pb + C.me2);
-  t->sms = C.hl[0] / pb;
-  t->eps = kb > 0.f ? 1.f : -1.f;
-  t->h0x = x0;
-  t->h0y = y0;
-  t->h0z = z0;
+  const float eps = kb > 0.f ? 1.f : -1.f;
+  const float rt = Rb * st;
   const float dx = x1 - x0, dy = y1 - y0;
   const float d = sqrtf(dx * dx + dy * dy);
   const float ex = dx / d, ey = dy / d;
   const float hd = 0.5f * d;
-  const float off = sqrtf(fmaxf((t->rt - hd) * (t->rt + hd), 0.f));
-  const float mx = 0.5f * (x0 + x1), my = 0.5f * (y0 + y1);
-  t->cx = mx + t->eps * ey * off;
-  t->cy = my - t->eps * ex * off;
-  t->ah0 = atan2f(y0 - t->cy, x0 - t->cx);
+  const float off = sqrtf(fmaxf((rt - hd) * (rt + hd), 0.f));
+  const float cx = 0.5f * (x0 + x1) + eps * ey * off;
+  const float cy = 0.5f * (y0 + y1) - eps * ex * off;
+  tr[0] = cx;
+  tr[1] = cy;
+  tr[2] = rt;
+  tr[3] = Rb;
+  tr[4] = ct;
+  tr[5] = st;
+  tr[6] = pb;
+  tr[7] = sqrtf(pb * pb + C.me2);
+  tr[8] = C.hl[0] / pb;
+  tr[9] = x0;
+  tr[10] = y0;
+  tr[11] = z0;
+  tr[12] = atan2f(y0 - cy, x0 - cx);
+  tr[13] = eps;
   return o;
+}
+
+// Track record layout (16 floats, also the global record of the staged form):
+// cx cy rt R ct st p E sms h0x h0y h0z ah0 eps - -
+template <int CK>
+__device__ __forceinline__ void store_track(TrkSoA<CK>& T, int k, const float* tr, int tid) {
+  T.cx[k] = tr[0];
+  T.cy[k] = tr[1];
+  T.rt[k] = tr[2];
+  T.R[k] = tr[3];
+  T.ct[k] = tr[4];
+  T.st[k] = tr[5];
+  T.p[k] = tr[6];
+  T.E[k] = tr[7];
+  T.sms[k] = tr[8];
+  T.h0x[k] = tr[9];
+  T.h0y[k] = tr[10];
+  T.h0z[k] = tr[11];
+  T.ah0[k] = tr[12];
+  T.eps[k] = tr[13];
+  T.tid[k] = tid;
 }
 
 // ------------------------------------------------------------------ vertex
 
-__device__ __forceinline__ float arc_to_h0(const TrkS& t, float x, float y) {
+struct TrackR {  // one kept track in registers (record layout above)
+  float cx, cy, rt, R, ct, st, p, E, sms, h0x, h0y, h0z, ah0, eps;
+};
+
+template <int CK>
+__device__ __forceinline__ TrackR load_track(const TrkSoA<CK>& T, int k) {
+  TrackR t;
+  t.cx = T.cx[k]; t.cy = T.cy[k]; t.rt = T.rt[k]; t.R = T.R[k]; t.ct = T.ct[k]; t.st = T.st[k];
+  t.p = T.p[k]; t.E = T.E[k]; t.sms = T.sms[k]; t.h0x = T.h0x[k]; t.h0y = T.h0y[k]; t.h0z = T.h0z[k];
+  t.ah0 = T.ah0[k]; t.eps = T.eps[k];
+  return t;
+}
+
+__device__ __forceinline__ TrackR load_track(const float4* __restrict__ rec, int64_t k) {
+  const float4 a = __ldg(rec + 4 * k), b = __ldg(rec + 4 * k + 1), c = __ldg(rec + 4 * k + 2),
+               d = __ldg(rec + 4 * k + 3);
+  TrackR t;
+  t.cx = a.x; t.cy = a.y; t.rt = a.z; t.R = a.w;
+  t.ct = b.x; t.st = b.y; t.p = b.z; t.E = b.w;
+  t.sms = c.x; t.h0x = c.y; t.h0y = c.z; t.h0z = c.w;
+  t.ah0 = d.x; t.eps = d.y;
+  return t;
+}
+
+// Turning angle travelled from point (x, y) forward to the track's layer-0 hit.
+__device__ __forceinline__ float arc_to_h0(const TrackR& t, float x, float y) {
   return wrap_2pi(t.eps * (atan2f(y - t.cy, x - t.cx) - t.ah0));
 }
 
-__device__ __forceinline__ float point_var(const TrkS& t, float x, float y, float sp2) {
+__device__ __forceinline__ float point_var(const TrackR& t, float x, float y, float sp2) {
   const float s = t.rt * arc_to_h0(t, x, y);
   return t.sms * t.sms * s * s + sp2;
 }
@@ -352,119 +452,120 @@ struct VtxOut {
   float chi2, tdist, ptot;
 };
 
+// Intersection points of the circles of tracks a and b, in two fixed slots (q0
+// first, as the oracle orders them), each with the target-filter flag and the
+// error sum of both tracks.  Returns 0 when the circles do not intersect.
+// Whether the transverse circles (centre, radius) of two tracks intersect, with
+// the distance D of the centres, the foot aa of the chord on the centre line and
+// the squared half chord h2 (one routine for the prefilter and the vertex).
+__device__ __forceinline__ bool circles_meet(float acx, float acy, float ar, float bcx, float bcy, float br, float& D,
+                                             float& aa, float& h2) {
+  const float ex = bcx - acx, ey = bcy - acy;
+  D = sqrtf(ex * ex + ey * ey);
+  if (!(D > 0.f)) return false;
+  aa = ((ar - br) * (ar + br) + D * D) / (2.f * D);
+  h2 = (ar - aa) * (ar + aa);
+  return !(h2 < 0.f);
+}
+
+__device__ __forceinline__ int pair_points(const TrackR& a, const TrackR& b, const DevCfg& C, float& x0, float& y0,
+                                           float& v0, bool& k0, float& x1, float& y1, float& v1, bool& k1) {
+  k0 = k1 = false;
+  v0 = v1 = 1.f;
+  float D, aa, h2;
+  if (!circles_meet(a.cx, a.cy, a.rt, b.cx, b.cy, b.rt, D, aa, h2)) return 0;
+  float ex = b.cx - a.cx, ey = b.cy - a.cy;
+  ex /= D;
+  ey /= D;
+  const float bx = a.cx + aa * ex, by = a.cy + aa * ey;
+  const float h = sqrtf(h2);
+  x0 = bx - h * ey;
+  y0 = by + h * ex;
+  x1 = bx + h * ey;
+  y1 = by - h * ex;
+  k0 = sqrtf(x0 * x0 + y0 * y0) <= C.isect_lim;
+  k1 = h2 != 0.f && sqrtf(x1 * x1 + y1 * y1) <= C.isect_lim;
+  if (k0) v0 = point_var(a, x0, y0, C.sig_pix2) + point_var(b, x0, y0, C.sig_pix2);
+  if (k1) v1 = point_var(a, x1, y1, C.sig_pix2) + point_var(b, x1, y1, C.sig_pix2);
+  return 1;
+}
+
+// Closest point of track t to (mx, my), its z on the helix and its error.  The
+// closest point lies on the ray from the centre through (mx, my), so its angle
+// seen from the centre is that of (mx - cx, my - cy).
+__device__ __forceinline__ void closest(const TrackR& t, float mx, float my, float sp2, float& px, float& py,
+                                        float& z, float& var, bool& bad) {
+  const float dx = mx - t.cx, dy = my - t.cy;
+  const float dn = sqrtf(dx * dx + dy * dy);
+  if (!(dn > 0.f)) bad = true;
+  const float sc = t.rt / dn;
+  px = t.cx + sc * dx;
+  py = t.cy + sc * dy;
+  const float dphi = wrap_2pi(t.eps * (atan2f(dy, dx) - t.ah0));
+  z = t.h0z - dphi * t.R * t.ct;
+  const float s = t.rt * dphi;
+  var = t.sms * t.sms * s * s + sp2;
+}
+
 // Vertex of one e+ e+ e- combination (Sec. "Vertex Fit", "Signal Estimation"):
 // pairwise circle intersections, target-disk filter, error-weighted transverse
-// mean for each choice of one point per pair, closest points, z projection,
-// chi2; the smallest-chi2 choice is cut on chi2, target distance and |sum p|.
-__device__ VtxOut vertex(const TrkS& A, const TrkS& B, const TrkS& E, const DevCfg& C) {
-  const TrkS* V[3] = {&A, &B, &E};
+// mean for each choice of one point per pair, closest points, z projection, chi2;
+// the smallest-chi2 choice is cut on chi2, target distance and |sum p|.  The loop
+// over the (at most 8) choices stays rolled: its body is large, and one copy keeps
+// the kernel's instruction footprint small.
+__device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const TrackR& E, const DevCfg& C) {
   VtxOut o;
-  o.status = 2;
+  o.status = 0;
   o.pass = 0;
   o.chi2 = o.tdist = o.ptot = FLT_MAX;
-  float px[3][2], py[3][2], pv[3][2];
-  int npt[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const TrkS& a = *V[k == 2 ? 1 : 0];
-    const TrkS& b = *V[k == 0 ? 1 : 2];
-    float ex = b.cx - a.cx, ey = b.cy - a.cy;
-    const float D = sqrtf(ex * ex + ey * ey);
-    npt[k] = 0;
-    if (!(D > 0.f)) {
-      o.status = 0;
-      return o;
-    }
-    const float aa = ((a.rt - b.rt) * (a.rt + b.rt) + D * D) / (2.f * D);
-    const float h2 = (a.rt - aa) * (a.rt + aa);
-    if (h2 < 0.f) {
-      o.status = 0;
-      return o;
-    }
-    ex /= D;
-    ey /= D;
-    const float bx = a.cx + aa * ex, by = a.cy + aa * ey;
-    const float h = sqrtf(h2);
-    const int nc = h2 == 0.f ? 1 : 2;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (j >= nc) break;
-      const float sg = j == 0 ? 1.f : -1.f;
-      const float qx = bx - sg * h * ey, qy = by + sg * h * ex;
-      if (sqrtf(qx * qx + qy * qy) > C.isect_lim) continue;
-      const int m = npt[k];
-      px[k][m] = qx;
-      py[k][m] = qy;
-      pv[k][m] = point_var(a, qx, qy, C.sig_pix2) + point_var(b, qx, qy, C.sig_pix2);
-      npt[k] = m + 1;
-    }
-  }
-  if (npt[0] == 0 || npt[1] == 0 || npt[2] == 0) {
-    o.status = 1;
-    return o;
-  }
-  float bmx = 0.f, bmy = 0.f, bmz = 0.f;
-  float bpx[3] = {0.f, 0.f, 0.f}, bpy[3] = {0.f, 0.f, 0.f};
-  float best = FLT_MAX;
+  float x00, y00, v00, x01, y01, v01, x10, y10, v10, x11, y11, v11, x20, y20, v20, x21, y21, v21;
+  bool k00, k01, k10, k11, k20, k21;
+  if (!pair_points(A, B, C, x00, y00, v00, k00, x01, y01, v01, k01)) return o;
+  if (!pair_points(A, E, C, x10, y10, v10, k10, x11, y11, v11, k11)) return o;
+  if (!pair_points(B, E, C, x20, y20, v20, k20, x21, y21, v21, k21)) return o;
+  o.status = 1;
+  if (!(k00 || k01) || !(k10 || k11) || !(k20 || k21)) return o;
+  float best = FLT_MAX, bmx = 0.f, bmy = 0.f, bmz = 0.f;
   bool have = false;
-#pragma unroll
+#pragma unroll 1
   for (int c = 0; c < 8; ++c) {
-    const int s0 = (c >> 2) & 1, s1 = (c >> 1) & 1, s2 = c & 1;  // s2 fastest
-    if (s0 >= npt[0] || s1 >= npt[1] || s2 >= npt[2]) continue;
-    const float w0 = 1.f / pv[0][s0], w1 = 1.f / pv[1][s1], w2 = 1.f / pv[2][s2];
-    const float ws = w0 + w1 + w2;
-    const float mx = (px[0][s0] * w0 + px[1][s1] * w1 + px[2][s2] * w2) / ws;
-    const float my = (py[0][s0] * w0 + py[1][s1] * w1 + py[2][s2] * w2) / ws;
-    float cx[3], cy[3], zi[3], vi[3];
+    const bool s0 = (c >> 2) & 1, s1 = (c >> 1) & 1, s2 = c & 1;  // s2 fastest, as the oracle's loops
+    if (!(s0 ? k01 : k00) || !(s1 ? k11 : k10) || !(s2 ? k21 : k20)) continue;
+    const float w0 = 1.f / (s0 ? v01 : v00), w1 = 1.f / (s1 ? v11 : v10), w2 = 1.f / (s2 ? v21 : v20);
+    const float iws = 1.f / (w0 + w1 + w2);
+    const float mx = ((s0 ? x01 : x00) * w0 + (s1 ? x11 : x10) * w1 + (s2 ? x21 : x20) * w2) * iws;
+    const float my = ((s0 ? y01 : y00) * w0 + (s1 ? y11 : y10) * w1 + (s2 ? y21 : y20) * w2) * iws;
+    float pa, qa, za, va, pb, qb, zb, vb, pe, qe, ze, ve;
     bool bad = false;
-    float wz = 0.f, wzs = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const TrkS& t = *V[i];
-      const float dx = mx - t.cx, dy = my - t.cy;
-      const float dn = sqrtf(dx * dx + dy * dy);
-      if (!(dn > 0.f)) bad = true;
-      cx[i] = t.cx + t.rt * dx / dn;
-      cy[i] = t.cy + t.rt * dy / dn;
-      const float dphi = arc_to_h0(t, cx[i], cy[i]);
-      zi[i] = t.h0z - dphi * t.R * t.ct;
-      const float s = t.rt * dphi;
-      vi[i] = t.sms * t.sms * s * s + C.sig_pix2;
-      wz += zi[i] / vi[i];
-      wzs += 1.f / vi[i];
-    }
+    closest(A, mx, my, C.sig_pix2, pa, qa, za, va, bad);
+    closest(B, mx, my, C.sig_pix2, pb, qb, zb, vb, bad);
+    closest(E, mx, my, C.sig_pix2, pe, qe, ze, ve, bad);
     if (bad) continue;
-    const float mz = wz / wzs;
-    float chi2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float dx = cx[i] - mx, dy = cy[i] - my, dz = zi[i] - mz;
-      chi2 += (dx * dx + dy * dy + dz * dz) / vi[i];
-    }
+    const float ia = 1.f / va, ib = 1.f / vb, ie = 1.f / ve;
+    const float mz = (za * ia + zb * ib + ze * ie) / (ia + ib + ie);
+    const float chi2 = ((pa - mx) * (pa - mx) + (qa - my) * (qa - my) + (za - mz) * (za - mz)) * ia +
+                       ((pb - mx) * (pb - mx) + (qb - my) * (qb - my) + (zb - mz) * (zb - mz)) * ib +
+                       ((pe - mx) * (pe - mx) + (qe - my) * (qe - my) + (ze - mz) * (ze - mz)) * ie;
     if (!have || chi2 < best) {
       have = true;
       best = chi2;
       bmx = mx;
       bmy = my;
       bmz = mz;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        bpx[i] = cx[i];
-        bpy[i] = cy[i];
-      }
     }
   }
-  if (!have || !isfinite(best)) {
-    o.status = 1;
-    return o;
-  }
+  if (!have || !isfinite(best)) return o;
+  o.status = 2;
   o.chi2 = best;
   o.tdist = target_distance(C, bmx, bmy, bmz);
   float Px = 0.f, Py = 0.f, Pz = 0.f;
+  const TrackR* V[3] = {&A, &B, &E};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const TrkS& t = *V[i];
-    const float ux = (bpx[i] - t.cx) / t.rt, uy = (bpy[i] - t.cy) / t.rt;
+    const TrackR& t = *V[i];
+    const float dx = bmx - t.cx, dy = bmy - t.cy;
+    const float idn = 1.f / sqrtf(dx * dx + dy * dy);
+    const float ux = dx * idn, uy = dy * idn;  // direction of the closest point from the centre
     const float pt = t.p * t.st;
     Px += pt * t.eps * uy;
     Py -= pt * t.eps * ux;
@@ -476,6 +577,7 @@ __device__ VtxOut vertex(const TrkS& A, const TrkS& B, const TrkS& E, const DevC
 }
 
 // ------------------------------------------------------------------ one frame
+
 
 template <class G>
 __device__ __forceinline__ void bucket_scan(const G& g, int* bcur, uint16_t* bstart) {
@@ -506,8 +608,13 @@ __device__ __forceinline__ void bucket_scan(const G& g, int* bcur, uint16_t* bst
   g.sync();
 }
 
-template <class G, class S, int CH, int CT, int CK, int CC, bool DEFER, bool DEBUG>
-__device__ int process_frame(const G& g, S& sm, const DevCfg& C, const KParams& P, int f) {
+constexpr int PENDING = -2;  // frame_front result: triplets selected, later stages to run
+
+// Stages A-C of one frame (load, sort, selection cuts).  Returns a final reason,
+// DEFERRED (frame too large for this stage), or PENDING with the selected
+// triplets in sm.u.trip and their count in sm.ntrip.
+template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG>
+__device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P, int f) {
   const bool stats = P.stats != nullptr;
   const int64_t base = P.off[f] - P.off_base;
   const int64_t n64 = P.off[f + 1] - P.off[f];
@@ -622,23 +729,31 @@ __device__ int process_frame(const G& g, S& sm, const DevCfg& C, const KParams& 
   if (ntrip > C.max_trip) return M3E_TRIPLET_OVERFLOW;
   if (DEFER && ntrip > CT) return DEFERRED;
   if (stats && g.leader()) sm.facc[ST_TRIP] += ntrip;
+  return PENDING;
+}
 
+// Stages D-F of one frame after frame_front returned PENDING: track
+// reconstruction, energy test and vertex.  Returns a final reason or DEFERRED.
+template <class G, class S, int CT, int CK, int CC, bool DEFER, bool DEBUG>
+__device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, int f) {
+  const bool stats = P.stats != nullptr;
+  const int ntrip = sm.ntrip;
+  const SmHits<S> view{sm};
   // ---- D: track reconstruction (Algorithm 3), one thread per triplet
   for (int t = g.rank(); t < ntrip; t += G::N) {
     const ushort4 tr = sm.u.trip[t];
-    TrkS tk;
-    const TrackOut o = build_track(sm, C, tr.x, tr.y, tr.z, &tk);
+    float tk[14];
+    const TrackOut o = build_track(view, C, tr.x, tr.y, tr.z, tk);
     if (o.status == 5) {
-      tk.tid = t;
       int slot = -1;
-      if (tk.eps > 0.f) {
+      if (tk[13] > 0.f) {
         const int k = atomicAdd(&sm.npos, 1);
         if (k < CK) slot = k;
       } else {
         const int k = atomicAdd(&sm.nneg, 1);
         if (k < CK) slot = CK - 1 - k;
       }
-      if (slot >= 0) sm.trk[slot] = tk;
+      if (slot >= 0) store_track(sm.t, slot, tk, t);
     }
     if (DEBUG && t < P.dump.cap_trip) {
       const int64_t r = (int64_t)f * P.dump.cap_trip + t;
@@ -660,24 +775,26 @@ __device__ int process_frame(const G& g, S& sm, const DevCfg& C, const KParams& 
   if (DEFER && ntrk > CK) return DEFERRED;
   if (stats && g.leader()) sm.facc[ST_TRK] += ntrk;
 
-  // ---- E: energy test of every (e+ pair, e-) combination (Algorithm 4, part 1)
+  // ---- E: energy test of every (e+ pair, e-) combination (Algorithm 4, part 1):
+  // one e+ pair per thread, the e- loop uniform across the group (broadcast reads)
   {
     const int npair = npos * (npos - 1) / 2;
-    const int ntest = npair * nneg;
-    for (int t = g.rank(); t < ntest; t += G::N) {
-      const int pr = t / nneg, c = t - pr * nneg;
+    for (int pr = g.rank(); pr < npair; pr += G::N) {
       int b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
       while (b * (b - 1) / 2 > pr) --b;
       while ((b + 1) * b / 2 <= pr) ++b;
       const int a = pr - b * (b - 1) / 2;
-      const int ci = CK - 1 - c;
-      const float e = sm.trk[a].E + sm.trk[b].E + sm.trk[ci].E - C.m_mu;
-      if (fabsf(e) <= C.e_win) {
-        const int k = atomicAdd(&sm.ncombo, 1);
-        if (k < CC) sm.u.combo[k] = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)ci << 16);
+      const float eab = sm.t.E[a] + sm.t.E[b];
+      for (int c = 0; c < nneg; ++c) {
+        const int ci = CK - 1 - c;
+        const float e = (eab + sm.t.E[ci]) - C.m_mu;
+        if (fabsf(e) <= C.e_win) {
+          const int k = atomicAdd(&sm.ncombo, 1);
+          if (k < CC) sm.u.combo[k] = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)ci << 16);
+        }
       }
     }
-    if (stats && g.leader()) sm.facc[ST_ETEST] += ntest;
+    if (stats && g.leader()) sm.facc[ST_ETEST] += (unsigned long long)npair * nneg;
   }
   g.sync();
   const int ncombo = sm.ncombo;
@@ -695,16 +812,16 @@ __device__ int process_frame(const G& g, S& sm, const DevCfg& C, const KParams& 
     if (c < ncombo) {
       const uint32_t cb = sm.u.combo[c];
       const int a = cb & 255, b = (cb >> 8) & 255, e = (cb >> 16) & 255;
-      const VtxOut v = vertex(sm.trk[a], sm.trk[b], sm.trk[e], C);
+      const VtxOut v = vertex(load_track(sm.t, a), load_track(sm.t, b), load_track(sm.t, e), C);
       pass = v.pass != 0;
       nv += v.status == 2;
       if (DEBUG && c < P.dump.cap_combo) {
         const int64_t r = (int64_t)f * P.dump.cap_combo + c;
-        P.dump.combo[4 * r + 0] = sm.trk[a].tid;
-        P.dump.combo[4 * r + 1] = sm.trk[b].tid;
-        P.dump.combo[4 * r + 2] = sm.trk[e].tid;
+        P.dump.combo[4 * r + 0] = sm.t.tid[a];
+        P.dump.combo[4 * r + 1] = sm.t.tid[b];
+        P.dump.combo[4 * r + 2] = sm.t.tid[e];
         P.dump.combo[4 * r + 3] = v.status | (v.pass << 8);
-        P.dump.combo_val[4 * r + 0] = sm.trk[a].E + sm.trk[b].E + sm.trk[e].E - C.m_mu;
+        P.dump.combo_val[4 * r + 0] = (sm.t.E[a] + sm.t.E[b] + sm.t.E[e]) - C.m_mu;
         P.dump.combo_val[4 * r + 1] = v.chi2;
         P.dump.combo_val[4 * r + 2] = v.tdist;
         P.dump.combo_val[4 * r + 3] = v.ptot;
@@ -717,7 +834,6 @@ __device__ int process_frame(const G& g, S& sm, const DevCfg& C, const KParams& 
   return found ? M3E_VERTEX : M3E_DROP;
 }
 
-// Store the frame's decision (store_frame of Algorithm 1) and commit its statistics.
 template <class G, class S>
 __device__ __forceinline__ void finish_frame(const G& g, S& sm, const KParams& P, int f, int r) {
   g.sync();
@@ -732,11 +848,11 @@ __device__ __forceinline__ void finish_frame(const G& g, S& sm, const KParams& P
 }
 
 template <class G, class S>
-__device__ __forceinline__ void flush_stats(const G& g, S& sm, const KParams& P) {
+__device__ __forceinline__ void flush_stats(const G& g, S& sm, unsigned long long* stats) {
   g.sync();
-  if (P.stats)
+  if (stats)
     for (int k = g.rank(); k < ST_REASON0 + 8; k += G::N)
-      if (sm.acc[k]) atomicAdd(P.stats + k, sm.acc[k]);
+      if (sm.acc[k]) atomicAdd(stats + k, sm.acc[k]);
 }
 
 template <class G, class S>
@@ -745,122 +861,5 @@ __device__ __forceinline__ void clear_stats(const G& g, S& sm) {
   g.sync();
 }
 
-// ------------------------------------------------------------------ kernels
-
-// Persistent warp-per-frame kernel: each warp takes `grab` frames at a time from
-// the device work queue; a frame that outgrows the warp's shared-memory stage is
-// appended to the deferred list for the CTA kernel.
-template <bool DEBUG>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
-    k_select_warp(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmWarp& sm = reinterpret_cast<SmWarp*>(smem_raw)[threadIdx.x >> 5];
-  const WarpGroup g;
-  clear_stats(g, sm);
-  const int nf = (int)P.n_frames;
-  for (;;) {
-    int f0 = 0;
-    if (g.leader()) f0 = atomicAdd(&P.work[0], P.grab);
-    f0 = __shfl_sync(FULL, f0, 0);
-    if (f0 >= nf) break;
-    const int f1 = min(f0 + P.grab, nf);
-    for (int f = f0; f < f1; ++f) {
-      const int r = process_frame<WarpGroup, SmWarp, W_HITS, W_TRIP, W_TRK, W_COMBO, true, DEBUG>(g, sm, C, P, f);
-      if (r == DEFERRED) {
-        if (g.leader()) {
-          const int k = atomicAdd(&P.work[1], 1);
-          P.defer_list[k] = f;
-          if (P.stats) sm.acc[ST_DEFER] += 1;
-        }
-      } else {
-        finish_frame(g, sm, P, f, r);
-      }
-      g.sync();
-    }
-  }
-  flush_stats(g, sm, P);
-}
-
-// CTA-per-frame kernel.  LIST: frames from the deferred list written by the warp
-// kernel earlier on the same stream; otherwise frames 0..n-1, one CTA each
-// (grid-stride when the grid is smaller).
-template <int NT, bool DEBUG, bool LIST>
-__global__ void __launch_bounds__(NT) k_select_cta(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmCta& sm = *reinterpret_cast<SmCta*>(smem_raw);
-  const CtaGroup<NT> g;
-  clear_stats(g, sm);
-  const int count = LIST ? P.work[1] : (int)P.n_frames;
-  for (int i = blockIdx.x; i < count; i += gridDim.x) {
-    const int f = LIST ? P.defer_list[i] : i;
-    const int r = process_frame<CtaGroup<NT>, SmCta, C_HITS, C_TRIP, C_TRK, C_COMBO, false, DEBUG>(g, sm, C, P, f);
-    finish_frame(g, sm, P, f, r);
-    g.sync();
-  }
-  flush_stats(g, sm, P);
-}
-
-template <class K>
-cudaError_t set_smem(K k, size_t bytes) {
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 }  // namespace
-
-size_t select_smem_bytes() { return sizeof(SmWarp) * WARPS_PER_CTA; }
-size_t cta_smem_bytes() { return sizeof(SmCta); }
-
-int select_blocks_per_sm() {
-  int nb = 0;
-  set_smem(k_select_warp<false>, select_smem_bytes());
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_select_warp<false>, WARPS_PER_CTA * 32,
-                                                    select_smem_bytes()) != cudaSuccess)
-    return 1;
-  return nb > 0 ? nb : 1;
-}
-
-cudaError_t launch_select(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s) {
-  const size_t sm = select_smem_bytes();
-  if (debug) {
-    cudaError_t e = set_smem(k_select_warp<true>, sm);
-    if (e != cudaSuccess) return e;
-    k_select_warp<true><<<grid, WARPS_PER_CTA * 32, sm, s>>>(c, p);
-  } else {
-    cudaError_t e = set_smem(k_select_warp<false>, sm);
-    if (e != cudaSuccess) return e;
-    k_select_warp<false><<<grid, WARPS_PER_CTA * 32, sm, s>>>(c, p);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_deferred(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s) {
-  const size_t sm = cta_smem_bytes();
-  if (debug) {
-    cudaError_t e = set_smem(k_select_cta<CTA_THREADS, true, true>, sm);
-    if (e != cudaSuccess) return e;
-    k_select_cta<CTA_THREADS, true, true><<<grid, CTA_THREADS, sm, s>>>(c, p);
-  } else {
-    cudaError_t e = set_smem(k_select_cta<CTA_THREADS, false, true>, sm);
-    if (e != cudaSuccess) return e;
-    k_select_cta<CTA_THREADS, false, true><<<grid, CTA_THREADS, sm, s>>>(c, p);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_plain(const DevCfg& c, const KParams& p, bool debug, cudaStream_t s) {
-  const size_t sm = cta_smem_bytes();
-  const int grid = (int)(p.n_frames < 0x7fffffff ? p.n_frames : 0x7fffffff);
-  if (grid == 0) return cudaSuccess;
-  if (debug) {
-    cudaError_t e = set_smem(k_select_cta<PLAIN_THREADS, true, false>, sm);
-    if (e != cudaSuccess) return e;
-    k_select_cta<PLAIN_THREADS, true, false><<<grid, PLAIN_THREADS, sm, s>>>(c, p);
-  } else {
-    cudaError_t e = set_smem(k_select_cta<PLAIN_THREADS, false, false>, sm);
-    if (e != cudaSuccess) return e;
-    k_select_cta<PLAIN_THREADS, false, false><<<grid, PLAIN_THREADS, sm, s>>>(c, p);
-  }
-  return cudaGetLastError();
-}
-
 }  // namespace m3e

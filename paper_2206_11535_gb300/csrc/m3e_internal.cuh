@@ -17,6 +17,7 @@ constexpr int DEFERRED = -1;      // process_frame result: frame too large for t
 // whose capacities are the configuration limits.
 constexpr int W_HITS = 160, W_TRIP = 160, W_TRK = 48, W_COMBO = 512;
 constexpr int C_HITS = 4096, C_TRIP = 1024, C_TRK = 128, C_COMBO = 1024;
+constexpr int S1_HITS = W_HITS;   // staged form: sorted-hit slot per frame (stage 1 defers larger frames)
 constexpr int WARPS_PER_CTA = 4;  // persistent warp kernel: warps (frames in flight) per CTA
 constexpr int CTA_THREADS = 256;  // large-frame kernel
 constexpr int PLAIN_THREADS = 128;  // plain per-frame kernel
@@ -35,6 +36,7 @@ struct DevCfg {
   float hl[4];                // Highland width numerator: sigma_MS(p) = hl[layer] / p
   float chi2_trk;
   float r3;
+  float colw3;                // one layer-3 column in phi plus rounding slack (4th-hit ring search)
   float me2, m_mu, e_win;
   float isect_lim;            // target_r + isect_margin
   float tgt_r, tgt_h, vtx_chi2, tgt_dist, ptot_max;
@@ -59,17 +61,37 @@ struct KParams {
   m3e_dump dump;              // all pointers null unless debugging
 };
 
+// Global scratch of the staged form (see m3e_staged.cu), sized per batch.
+struct SParams {
+  float *hx, *hy, *hz, *hphi;  // sorted hits of each pending frame, slot f * S1_HITS
+  uint32_t* haddr;
+  uint16_t* hidx;              // input index of each sorted hit (candidate record only)
+  uint16_t* l3;                // [F][NB + 1] layer-3 phi-bin starts, frame-relative
+  int *fstate, *ftbase, *fntrip, *ffound;  // per frame: state, triplet range, vertex found
+  long long* fcbase;           // per frame: first combination
+  int* fncombo;
+  int4* trip;                  // {frame, i0, i1, i2} (frame-relative sorted indices), frame -1 = unused
+  uint8_t* tstatus;            // per triplet: track status
+  float4* trec;                // per triplet: 16-float track record when kept
+  int4* combo;                 // {frame, triplet a, triplet b, triplet e-}, frame -1 = unused
+  unsigned long long* counters;  // [0] triplets appended, [1] combinations appended, [2] stage-3 queue
+  int64_t trip_cap, combo_cap;
+};
+
 enum { ST_FRAMES = 0, ST_HITS, ST_PAIRS, ST_TTESTS, ST_TRIP, ST_TRK, ST_ETEST, ST_COMBO, ST_VTX, ST_DEFER,
        ST_REASON0 };
 
 enum { ERR_BADHIT = 1, ERR_NEGSIZE = 2 };
 
-// Host-side launchers (m3e_kernels.cu).
-cudaError_t launch_select(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
+// Host-side launchers (m3e_fused.cu, m3e_staged.cu).
+cudaError_t launch_fused(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
 cudaError_t launch_deferred(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
 cudaError_t launch_plain(const DevCfg& c, const KParams& p, bool debug, cudaStream_t s);
-int select_blocks_per_sm();
-size_t select_smem_bytes();
+cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[4], bool debug,
+                          cudaStream_t st, cudaEvent_t* ev);
+int fused_blocks_per_sm();
+int stage_blocks_per_sm(int stage);
+size_t fused_smem_bytes();
 size_t cta_smem_bytes();
 
 }  // namespace m3e

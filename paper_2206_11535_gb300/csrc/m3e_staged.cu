@@ -1,0 +1,451 @@
+// Staged selection kernels of libm3e: the same method as the fused kernels,
+// with the work of a batch regrouped by candidate instead of by frame.
+//   stage 1  warp per frame: decode, phi-bin sort, selection cuts (Algorithm 2);
+//            the sorted hits and the selected triplets go to global memory
+//   stage 2  thread per triplet of the whole batch: track reconstruction (Algorithm 3)
+//   stage 3  warp per frame: track cap, energy test (Algorithm 4, part 1);
+//            combinations go to global memory
+//   stage 4  thread per combination of the whole batch: vertex (Algorithm 4, part 2)
+//   stage 5  thread per frame: decision (store_frame of Algorithm 1)
+// Every kernel is small and runs one kind of work, so warps share their
+// instructions and lanes; a frame's candidates stay contiguous, so its hits and
+// tracks are read from L2 by neighbouring threads.  Frames that exceed a stage's
+// capacity are deferred to the CTA-per-frame kernel with identical decisions.
+#include "m3e_device.cuh"
+
+namespace m3e {
+namespace {
+
+constexpr int NL3 = NB + 1;                        // layer-3 bin starts per frame
+constexpr int S1_TRIP = 256;                       // stage-1 triplet capacity (hits: S1_HITS)
+using SmFront = FrameSm<S1_HITS, S1_TRIP, 1, 1>;
+constexpr int S3_WARPS = 4;
+
+struct S3Sm {                                      // stage 3, per warp
+  int pidx[C_TRK], nidx[C_TRK];                    // triplet index of each e+ / e- track
+  float pE[C_TRK], nE[C_TRK];
+  int npos, nneg;
+  unsigned long long acc[ST_REASON0 + 8];
+};
+
+__device__ __forceinline__ int warp_count_add(int* ctr, bool pred) {  // ordered warp compaction
+  const unsigned m = __ballot_sync(FULL, pred);
+  int base = 0;
+  if ((threadIdx.x & 31) == 0 && m) base = atomicAdd(ctr, __popc(m));
+  base = __shfl_sync(FULL, base, 0);
+  return base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+}
+
+// ---- stage 1
+template <bool DEBUG>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
+    k_stage1(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmFront& sm = reinterpret_cast<SmFront*>(smem_raw)[threadIdx.x >> 5];
+  const WarpGroup g;
+  clear_stats(g, sm);
+  const int nf = (int)P.n_frames;
+  for (;;) {
+    int f0 = 0;
+    if (g.leader()) f0 = atomicAdd(&P.work[0], P.grab);
+    f0 = __shfl_sync(FULL, f0, 0);
+    if (f0 >= nf) break;
+    const int f1 = min(f0 + P.grab, nf);
+    for (int f = f0; f < f1; ++f) {
+      int r = frame_front<WarpGroup, SmFront, S1_HITS, S1_TRIP, true, DEBUG>(g, sm, C, P, f);
+      const int ntrip = sm.ntrip;
+      if (r == PENDING && ntrip == 0) r = M3E_DROP;  // no triplet: no track, no vertex
+      if (r == PENDING) {
+        long long tb = 0;
+        if (g.leader()) tb = (long long)atomicAdd(&S.counters[0], (unsigned long long)ntrip);
+        tb = __shfl_sync(FULL, tb, 0);
+        if (tb + ntrip > S.trip_cap) {
+          // out of candidate space: mark the slots this frame owns below the cap, defer
+          for (int64_t t = tb + g.rank(); t < S.trip_cap; t += 32) S.trip[t] = make_int4(-1, 0, 0, 0);
+          r = DEFERRED;
+        } else {
+          const int64_t base = (int64_t)f * S1_HITS;
+          const int n = (int)(P.off[f + 1] - P.off[f]);
+          for (int i = g.rank(); i < n; i += 32) {
+            S.hx[base + i] = sm.x[i];
+            S.hy[base + i] = sm.y[i];
+            S.hz[base + i] = sm.z[i];
+            S.hphi[base + i] = sm.phi[i];
+            S.haddr[base + i] = sm.addr[i];
+            if (DEBUG) S.hidx[base + i] = sm.inidx[i];
+          }
+          for (int b = g.rank(); b < NL3; b += 32) S.l3[(int64_t)f * NL3 + b] = sm.bstart[3 * NB + b];
+          for (int t = g.rank(); t < ntrip; t += 32) {
+            const ushort4 q = sm.u.trip[t];
+            S.trip[tb + t] = make_int4(f, q.x, q.y, q.z);
+          }
+          if (g.leader()) {
+            S.fstate[f] = PENDING;
+            S.ftbase[f] = (int)tb;
+            S.fntrip[f] = ntrip;
+            S.ffound[f] = 0;
+            if (P.stats)
+              for (int k = 0; k < ST_REASON0; ++k) sm.acc[k] += sm.facc[k];
+          }
+        }
+      }
+      if (r == DEFERRED) {
+        if (g.leader()) {
+          S.fstate[f] = DEFERRED;
+          const int k = atomicAdd(&P.work[1], 1);
+          P.defer_list[k] = f;
+          if (P.stats) sm.acc[ST_DEFER] += 1;
+        }
+      } else if (r != PENDING) {
+        if (g.leader()) S.fstate[f] = r;
+        finish_frame(g, sm, P, f, r);
+      }
+      g.sync();
+    }
+  }
+  flush_stats(g, sm, P.stats);
+}
+
+// ---- stage 2: one thread per selected triplet
+template <bool DEBUG>
+__global__ void __launch_bounds__(128)
+    k_stage2(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
+  const int64_t n = min((int64_t)S.counters[0], S.trip_cap);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 r = S.trip[i];
+    const int f = r.x;
+    if (f < 0) continue;
+    const int64_t base = (int64_t)f * S1_HITS;
+    const GHits v{S.hx + base, S.hy + base, S.hz + base, S.hphi + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
+    float tk[14];
+    const TrackOut o = build_track(v, C, r.y, r.z, r.w, tk);
+    S.tstatus[i] = (uint8_t)o.status;
+    if (o.status == 5) {
+      float4* q = S.trec + 4 * i;
+      q[0] = make_float4(tk[0], tk[1], tk[2], tk[3]);
+      q[1] = make_float4(tk[4], tk[5], tk[6], tk[7]);
+      q[2] = make_float4(tk[8], tk[9], tk[10], tk[11]);
+      q[3] = make_float4(tk[12], tk[13], 0.f, 0.f);
+    }
+    if (DEBUG) {
+      const int t = (int)(i - S.ftbase[f]);
+      if (t < P.dump.cap_trip) {
+        const int64_t d = (int64_t)f * P.dump.cap_trip + t;
+        P.dump.trip[4 * d + 0] = S.hidx[base + r.y];
+        P.dump.trip[4 * d + 1] = S.hidx[base + r.z];
+        P.dump.trip[4 * d + 2] = S.hidx[base + r.w];
+        P.dump.trip[4 * d + 3] = o.i3 >= 0 ? (int)S.hidx[base + o.i3] : -1;
+        P.dump.trk_status[d] = o.status;
+        P.dump.trk_val[4 * d + 0] = o.kbar;
+        P.dump.trk_val[4 * d + 1] = o.th01;
+        P.dump.trk_val[4 * d + 2] = o.chi2;
+        P.dump.trk_val[4 * d + 3] = o.mbest;
+      }
+    }
+  }
+}
+
+// ---- stage 3: warp per frame, track cap and energy test
+template <bool DEBUG>
+__global__ void __launch_bounds__(S3_WARPS * 32)
+    k_stage3(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
+  __shared__ S3Sm smem[S3_WARPS];
+  S3Sm& sm = smem[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k < ST_REASON0 + 8; k += 32) sm.acc[k] = 0;
+  __syncwarp();
+  const int nf = (int)P.n_frames;
+  const bool stats = P.stats != nullptr;
+  for (;;) {
+    int f0 = 0;
+    if (lane == 0) f0 = (int)atomicAdd(&S.counters[2], (unsigned long long)P.grab);
+    f0 = __shfl_sync(FULL, f0, 0);
+    if (f0 >= nf) break;
+    const int f1 = min(f0 + P.grab, nf);
+    for (int f = f0; f < f1; ++f) {
+      if (S.fstate[f] != PENDING) continue;
+      const int tb = S.ftbase[f], nt = S.fntrip[f];
+      if (lane == 0) {
+        sm.npos = 0;
+        sm.nneg = 0;
+      }
+      __syncwarp();
+      // kept tracks of the frame's triplets, split by charge
+      for (int t0 = 0; t0 < nt; t0 += 32) {
+        const int t = t0 + lane;
+        const bool kept = t < nt && S.tstatus[tb + t] == 5;
+        float eps = 0.f, E = 0.f;
+        if (kept) {
+          const float4 q1 = __ldg(S.trec + 4 * (int64_t)(tb + t) + 1);
+          const float4 q3 = __ldg(S.trec + 4 * (int64_t)(tb + t) + 3);
+          E = q1.w;
+          eps = q3.y;
+        }
+        const bool pos = kept && eps > 0.f, neg = kept && !(eps > 0.f);
+        const int kp = warp_count_add(&sm.npos, pos);
+        const int kn = warp_count_add(&sm.nneg, neg);
+        if (pos && kp < C_TRK) {
+          sm.pidx[kp] = tb + t;
+          sm.pE[kp] = E;
+        }
+        if (neg && kn < C_TRK) {
+          sm.nidx[kn] = tb + t;
+          sm.nE[kn] = E;
+        }
+        __syncwarp();
+      }
+      __syncwarp();
+      const int npos = sm.npos, nneg = sm.nneg;
+      int r = PENDING;
+      if (npos + nneg > C.max_trk) r = M3E_TRACK_OVERFLOW;
+      const int npair = npos * (npos - 1) / 2;
+      int ncombo = 0;
+      if (r == PENDING) {
+        if (stats && lane == 0) {
+          sm.acc[ST_TRK] += npos + nneg;
+          sm.acc[ST_ETEST] += (unsigned long long)npair * nneg;
+        }
+        // pass 1: count the combinations passing the energy test
+        for (int p0 = 0; p0 < npair; p0 += 32) {
+          const int pr = p0 + lane;
+          int cnt = 0;
+          if (pr < npair) {
+            int b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
+            while (b * (b - 1) / 2 > pr) --b;
+            while ((b + 1) * b / 2 <= pr) ++b;
+            const int a = pr - b * (b - 1) / 2;
+            const float eab = sm.pE[a] + sm.pE[b];
+            for (int c = 0; c < nneg; ++c) cnt += fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
+          }
+          ncombo += __reduce_add_sync(FULL, cnt);
+        }
+        if (DEBUG && lane == 0) P.dump.n_combo[f] = ncombo;
+        if (ncombo > C.max_combo) r = M3E_COMBO_OVERFLOW;
+        else if (ncombo == 0) r = M3E_DROP;
+      }
+      if (r == PENDING) {
+        long long cb = 0;
+        if (lane == 0) cb = (long long)atomicAdd(&S.counters[1], (unsigned long long)ncombo);
+        cb = __shfl_sync(FULL, cb, 0);
+        if (cb + ncombo > S.combo_cap) {
+          for (int64_t t = cb + lane; t < S.combo_cap; t += 32) S.combo[t] = make_int4(-1, 0, 0, 0);
+          r = DEFERRED;
+        } else {
+          // pass 2: write them, in (pair, e-) order
+          long long w = cb;
+          for (int p0 = 0; p0 < npair; p0 += 32) {
+            const int pr = p0 + lane;
+            int a = 0, b = 0;
+            float eab = 0.f;
+            const bool act = pr < npair;
+            if (act) {
+              b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
+              while (b * (b - 1) / 2 > pr) --b;
+              while ((b + 1) * b / 2 <= pr) ++b;
+              a = pr - b * (b - 1) / 2;
+              eab = sm.pE[a] + sm.pE[b];
+            }
+            for (int c = 0; c < nneg; ++c) {
+              const bool pass = act && fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
+              const unsigned m = __ballot_sync(FULL, pass);
+              if (pass) S.combo[w + __popc(m & ((1u << lane) - 1u))] = make_int4(f, sm.pidx[a], sm.pidx[b], sm.nidx[c]);
+              w += __popc(m);
+            }
+          }
+          if (lane == 0) {
+            S.fcbase[f] = cb;
+            S.fncombo[f] = ncombo;
+            if (stats) sm.acc[ST_COMBO] += ncombo;
+          }
+        }
+      }
+      if (r == DEFERRED) {
+        if (lane == 0) {
+          S.fstate[f] = DEFERRED;
+          const int k = atomicAdd(&P.work[1], 1);
+          P.defer_list[k] = f;
+          if (stats) sm.acc[ST_DEFER] += 1;
+        }
+      } else if (r != PENDING) {
+        if (lane == 0) {
+          S.fstate[f] = r;
+          P.keep[f] = (uint8_t)(r != M3E_DROP);
+          P.reason[f] = (uint8_t)r;
+          if (stats) sm.acc[ST_REASON0 + r] += 1;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  if (stats)
+    for (int k = lane; k < ST_REASON0 + 8; k += 32)
+      if (sm.acc[k]) atomicAdd(P.stats + k, sm.acc[k]);
+}
+
+// ---- stage 4: vertex of every combination, compacted per warp
+// About three quarters of the combinations fail at the first step (a pair of
+// track circles that does not intersect).  Each warp therefore tests 32
+// combinations at a time for that, appends the survivors to a queue in shared
+// memory, and runs the full vertex on 32 queued survivors at a time, so that all
+// lanes do the expensive part together.
+constexpr int S4_WARPS = 4;
+
+__device__ __forceinline__ void load_circle(const float4* __restrict__ rec, int64_t k, float& cx, float& cy,
+                                            float& rt) {
+  const float4 a = __ldg(rec + 4 * k);
+  cx = a.x;
+  cy = a.y;
+  rt = a.z;
+}
+
+template <bool DEBUG>
+__device__ __forceinline__ void stage4_dump(const DevCfg& C, const KParams& P, const SParams& S, int64_t i,
+                                            const int4& r, const VtxOut& v, float esum) {
+  const int f = r.x;
+  const int c = (int)(i - S.fcbase[f]);
+  if (c < P.dump.cap_combo) {
+    const int64_t d = (int64_t)f * P.dump.cap_combo + c;
+    const int tb = S.ftbase[f];
+    P.dump.combo[4 * d + 0] = r.y - tb;
+    P.dump.combo[4 * d + 1] = r.z - tb;
+    P.dump.combo[4 * d + 2] = r.w - tb;
+    P.dump.combo[4 * d + 3] = v.status | (v.pass << 8);
+    P.dump.combo_val[4 * d + 0] = esum - C.m_mu;
+    P.dump.combo_val[4 * d + 1] = v.chi2;
+    P.dump.combo_val[4 * d + 2] = v.tdist;
+    P.dump.combo_val[4 * d + 3] = v.ptot;
+  }
+}
+
+template <bool DEBUG>
+__global__ void __launch_bounds__(S4_WARPS * 32)
+    k_stage4(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
+  __shared__ long long queue[S4_WARPS][64];
+  long long* q = queue[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int64_t n = min((int64_t)S.counters[1], S.combo_cap);
+  const int64_t stride = (int64_t)gridDim.x * S4_WARPS * 32;
+  int qn = 0;
+  unsigned nv = 0;
+  for (int64_t base = ((int64_t)blockIdx.x * S4_WARPS + (threadIdx.x >> 5)) * 32;; base += stride) {
+    const bool more = base < n;  // uniform in the warp
+    if (more) {
+      const int64_t i = base + lane;
+      bool cand = false;
+      if (i < n) {
+        const int4 r = S.combo[i];
+        const int f = r.x;
+        if (f >= 0 && S.fstate[f] == PENDING && (DEBUG || !*((volatile int*)S.ffound + f))) {
+          float ax, ay, ar, bx, by, br, ex, ey, er, D, aa, h2;
+          load_circle(S.trec, r.y, ax, ay, ar);
+          load_circle(S.trec, r.z, bx, by, br);
+          load_circle(S.trec, r.w, ex, ey, er);
+          cand = circles_meet(ax, ay, ar, bx, by, br, D, aa, h2) && circles_meet(ax, ay, ar, ex, ey, er, D, aa, h2) &&
+                 circles_meet(bx, by, br, ex, ey, er, D, aa, h2);
+          if (DEBUG && !cand) {  // record the combination with status 0 (no intersection)
+            VtxOut v;
+            v.status = 0;
+            v.pass = 0;
+            v.chi2 = v.tdist = v.ptot = FLT_MAX;
+            const float4 qa = __ldg(S.trec + 4 * (int64_t)r.y + 1), qb = __ldg(S.trec + 4 * (int64_t)r.z + 1),
+                         qe = __ldg(S.trec + 4 * (int64_t)r.w + 1);
+            stage4_dump<DEBUG>(C, P, S, i, r, v, qa.w + qb.w + qe.w);
+          }
+        }
+      }
+      const unsigned m = __ballot_sync(FULL, cand);
+      if (cand) q[qn + __popc(m & ((1u << lane) - 1u))] = i;
+      qn += __popc(m);
+    }
+    __syncwarp();
+    while (qn >= 32 || (!more && qn > 0)) {
+      const int take = qn < 32 ? qn : 32;
+      if (lane < take) {
+        const int64_t i = q[qn - take + lane];
+        const int4 r = S.combo[i];
+        const TrackR A = load_track(S.trec, r.y), B = load_track(S.trec, r.z), E = load_track(S.trec, r.w);
+        const VtxOut v = vertex(A, B, E, C);
+        nv += v.status == 2;
+        if (v.pass) S.ffound[r.x] = 1;
+        if (DEBUG) stage4_dump<DEBUG>(C, P, S, i, r, v, A.E + B.E + E.E);
+      }
+      qn -= take;
+      __syncwarp();
+    }
+    if (!more) break;
+  }
+  if (P.stats) {
+    const unsigned s = __reduce_add_sync(FULL, nv);
+    if (lane == 0 && s) atomicAdd(P.stats + ST_VTX, (unsigned long long)s);
+  }
+}
+
+// ---- stage 5: decision of the frames still pending
+__global__ void __launch_bounds__(256)
+    k_stage5(const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
+  __shared__ unsigned cnt[2];
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < P.n_frames && S.fstate[f] == PENDING) {
+    const int r = S.ffound[f] ? M3E_VERTEX : M3E_DROP;
+    P.keep[f] = (uint8_t)(r != M3E_DROP);
+    P.reason[f] = (uint8_t)r;
+    if (P.stats) atomicAdd(&cnt[r], 1u);
+  }
+  __syncthreads();
+  if (P.stats && threadIdx.x < 2 && cnt[threadIdx.x])
+    atomicAdd(P.stats + ST_REASON0 + threadIdx.x, (unsigned long long)cnt[threadIdx.x]);
+}
+
+template <class K>
+cudaError_t set_smem(K k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t stage1_smem_bytes() { return sizeof(SmFront) * WARPS_PER_CTA; }
+
+int stage_blocks_per_sm(int stage) {
+  int nb = 0;
+  cudaError_t e = cudaSuccess;
+  if (stage == 1) {
+    set_smem(k_stage1<false>, stage1_smem_bytes());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1<false>, WARPS_PER_CTA * 32, stage1_smem_bytes());
+  } else if (stage == 2) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage2<false>, 128, 0);
+  } else if (stage == 3) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage3<false>, S3_WARPS * 32, 0);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage4<false>, S4_WARPS * 32, 0);
+  }
+  return e == cudaSuccess && nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[4], bool debug,
+                          cudaStream_t st, cudaEvent_t* ev) {
+  const size_t sm1 = stage1_smem_bytes();
+  cudaError_t e = debug ? set_smem(k_stage1<true>, sm1) : set_smem(k_stage1<false>, sm1);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (debug) k_stage1<true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p, s);
+  else k_stage1<false><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p, s);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (debug) k_stage2<true><<<grids[1], 128, 0, st>>>(c, p, s);
+  else k_stage2<false><<<grids[1], 128, 0, st>>>(c, p, s);
+  if (ev) cudaEventRecord(ev[2], st);
+  if (debug) k_stage3<true><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p, s);
+  else k_stage3<false><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p, s);
+  if (ev) cudaEventRecord(ev[3], st);
+  if (debug) k_stage4<true><<<grids[3], S4_WARPS * 32, 0, st>>>(c, p, s);
+  else k_stage4<false><<<grids[3], S4_WARPS * 32, 0, st>>>(c, p, s);
+  if (ev) cudaEventRecord(ev[4], st);
+  const int g5 = (int)((p.n_frames + 255) / 256);
+  if (g5 > 0) k_stage5<<<g5, 256, 0, st>>>(p, s);
+  if (ev) cudaEventRecord(ev[5], st);
+  return cudaGetLastError();
+}
+
+}  // namespace m3e

@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libm3e.so")
 
 OK, EINVAL, ENOMEM, EBADHIT, ECUDA, EBUSY, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+STAGED, FUSED, PLAIN = 0, 1, 2  # forms of the selection (m3e_select_frames_debug)
 DROP, VERTEX, TRIPLET_OVERFLOW, TRACK_OVERFLOW, COMBO_OVERFLOW, HIT_OVERFLOW, ERR_BADHIT = range(7)
 REASONS = ("DROP", "VERTEX", "TRIPLET_OVERFLOW", "TRACK_OVERFLOW", "COMBO_OVERFLOW", "HIT_OVERFLOW", "ERR_BADHIT")
 
@@ -54,17 +55,18 @@ class Dump(C.Structure):
                 ("n_combo", C.c_void_p), ("combo", C.c_void_p), ("combo_val", C.c_void_p)]
 
 
-def _load():
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2206_11535_gb300.build.build() "
+def _load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2206_11535_gb300.build.build() "
                            "(the selection has no CPU path)")
-    lib = C.CDLL(LIB_PATH)
+    lib = C.CDLL(path)
     vp, i64 = C.c_void_p, C.c_int64
     lib.m3e_create.argtypes = [C.POINTER(Config), C.c_int, C.POINTER(vp)]
     lib.m3e_destroy.argtypes = [vp]
-    for name in ("m3e_select_frames", "m3e_select_frames_plain"):
+    for name in ("m3e_select_frames", "m3e_select_frames_fused", "m3e_select_frames_plain"):
         getattr(lib, name).argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
-    lib.m3e_select_frames_debug.argtypes = [vp, vp, vp, i64, vp, vp, C.POINTER(Dump), vp]
+    lib.m3e_select_frames_debug.argtypes = [vp, C.c_int, vp, vp, i64, vp, vp, C.POINTER(Dump), vp]
+    lib.m3e_stage_times.argtypes = [vp, C.POINTER(C.c_float), C.c_int]
     lib.m3e_select_frames_host.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.m3e_check.argtypes = [vp, vp]
     lib.m3e_set_launch.argtypes = [vp, C.c_int, C.c_int]
@@ -174,6 +176,13 @@ class Context:
                                      _stream(stream)))
         return keep, reason
 
+    def select_frames_fused(self, hits, off, keep=None, reason=None, stats=None, stream=None):
+        """``m3e_select_frames_fused``: one persistent kernel, a warp per frame."""
+        nf, keep, reason = self._outs(hits, off, keep, reason)
+        _check(lib.m3e_select_frames_fused(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
+                                           _ptr(stats), _stream(stream)))
+        return keep, reason
+
     def select_frames_plain(self, hits, off, keep=None, reason=None, stats=None, stream=None):
         """``m3e_select_frames_plain``: one CTA per frame, one launch per batch."""
         nf, keep, reason = self._outs(hits, off, keep, reason)
@@ -181,9 +190,10 @@ class Context:
                                            _ptr(stats), _stream(stream)))
         return keep, reason
 
-    def select_frames_debug(self, hits, off, cap_trip=768, cap_combo=1024, stream=None):
-        """``m3e_select_frames_debug``: returns keep, reason and the candidate record
-        (torch tensors on the device, frame-major)."""
+    def select_frames_debug(self, hits, off, cap_trip=768, cap_combo=1024, stream=None, form=STAGED):
+        """``m3e_select_frames_debug`` through ``form`` (STAGED, FUSED or PLAIN):
+        returns keep, reason and the candidate record (torch tensors on the device,
+        frame-major)."""
         import torch
         nf, keep, reason = self._outs(hits, off, None, None)
         dev = off.device
@@ -196,7 +206,7 @@ class Context:
                    combo_val=torch.zeros((nf, cap_combo, 4), dtype=torch.float32, device=dev))
         d = Dump(cap_trip, cap_combo, *[_ptr(rec[k]) for k in ("n_trip", "trip", "trk_status", "trk_val", "n_combo",
                                                                   "combo", "combo_val")])
-        _check(lib.m3e_select_frames_debug(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
+        _check(lib.m3e_select_frames_debug(self._h, form, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
                                            C.byref(d), _stream(stream)))
         rec["keep"], rec["reason"] = keep, reason
         return rec
@@ -227,6 +237,12 @@ class Context:
 
     def set_profiling(self, on: bool = True):
         _check(lib.m3e_set_profiling(self._h, int(on)))
+
+    def stage_times(self) -> list[float]:
+        """ms of stages 1-5 and of the deferred-frame kernel of the last timed staged call."""
+        a = (C.c_float * 6)()
+        _check(lib.m3e_stage_times(self._h, a, 6))
+        return list(a)
 
     def kernel_times(self) -> tuple[float, float]:
         """(main kernel ms, deferred-frame kernel ms) of the last timed select call."""

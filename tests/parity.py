@@ -83,19 +83,24 @@ def compare_frame(c, hits_f, g: dict, f: int) -> FrameResult:
         (R.bounds if b else R.fails).append(("triplet", t, "oracle" if t in o_trip else "gpu", v.tolist()))
     # ---------------- tracks of the common triplets
     bad_trk = set()
+    addr = lambda i: int(hits_f[i]) if i >= 0 else -1  # noqa: E731
     for t in set(o_trip) & set(g_trip):
         ot = o["tracks"][o_trip[t]]
         gs = int(g["trk_status"][g_trip[t]])
+        # the 4th hit is compared by pixel address: among duplicated addresses (distinct
+        # hits, identical positions) either choice gives the same track
         gi3 = int(g["trip"][g_trip[t], 3])
+        gi3 = next((j for j in range(len(hits_f)) if addr(j) == addr(gi3)), gi3) if gi3 >= 0 else gi3
+        oi3 = next((j for j in range(len(hits_f)) if addr(j) == addr(ot.i[3])), -1) if ot.i[3] >= 0 else -1
         kb, th, chi2, mb = (float(x) for x in g["trk_val"][g_trip[t]])
         tie = (ot.m_second - ot.m_best) <= DERIVED_REL * (1.0 + ot.m_best)
-        if ot.status != gs or (ot.status >= 3 and ot.i[3] != gi3):
+        if ot.status != gs or (ot.status >= 3 and oi3 != gi3):
             why = []
-            if ot.i[3] != gi3 and tie:
+            if oi3 != gi3 and tie:
                 why.append("4th-hit tie")
             if {ot.status, gs} == {4, 5} and _near(ot.chi2, c.chi2_track_max, DERIVED_REL):
                 why.append("chi2 at cut")
-            (R.bounds if why else R.fails).append(("track", t, ot.status, gs, ot.i[3], gi3, why, ot.chi2, chi2))
+            (R.bounds if why else R.fails).append(("track", t, ot.status, gs, oi3, gi3, why, ot.chi2, chi2))
             bad_trk.add(t)
             continue
         if gs == 5:  # a kept track: its fitted values (rejected fits only carry the chi2 decision)
@@ -114,11 +119,15 @@ def compare_frame(c, hits_f, g: dict, f: int) -> FrameResult:
             R.fails.append(("reason", o["reason"], int(g["reason"])))
         return _finish(R)
     # ---------------- combinations
-    o_trkkey = [tuple(o["tracks"][ti].i) for ti in o["kept"]]
+    first = {}
+    for j in range(len(hits_f)):
+        first.setdefault(int(hits_f[j]), j)
+    canon = lambda i: first[int(hits_f[i])] if i >= 0 else -1  # noqa: E731
+    o_trkkey = [tuple(o["tracks"][ti].i[:3]) + (canon(o["tracks"][ti].i[3]),) for ti in o["kept"]]
     def okey(cb):
         a, b, e = (o_trkkey[k] for k in cb.t)
         return (tuple(sorted([a, b])), e)
-    g_tripkey = {k: tuple(int(x) for x in g["trip"][k]) for k in g_trip.values()}
+    g_tripkey = {k: tuple(int(x) for x in g["trip"][k, :3]) + (canon(int(g["trip"][k, 3])),) for k in g_trip.values()}
     def gkey(row):
         a, b, e = (g_tripkey.get(int(k), ("?",)) for k in row[:3])
         return (tuple(sorted([a, b])), e)

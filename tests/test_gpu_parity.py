@@ -44,28 +44,33 @@ def _check_results(res, max_boundary_frac=0.01):
     return s
 
 
-def test_c1_parity_all_frames(ctx, ocfg):
-    """1,000 frames of the parity workload: every candidate list and decision."""
+FORMS = {"staged": 0, "fused": 1, "plain": 2}
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_c1_parity_all_frames(ctx, ocfg, form):
+    """1,000 frames of the parity workload, every candidate list and decision, for
+    each form of the selection."""
     d = gen.workload("c1")
     hits, off = _dev(d)
-    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024))
+    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024, form=FORMS[form]))
     s = _check_results(P.compare_batch(ocfg, d["hits"], d["off"], rec))
-    print("c1 parity", s)
-    keep, reason = ctx.select_frames(hits, off)
+    print("c1 parity", form, s)
+    entry = {"staged": ctx.select_frames, "fused": ctx.select_frames_fused, "plain": ctx.select_frames_plain}[form]
+    keep, reason = entry(hits, off)
     assert (reason.cpu().numpy() == rec["reason"]).all()
     assert (keep.cpu().numpy() == rec["keep"]).all()
-    keep_p, reason_p = ctx.select_frames_plain(hits, off)
-    assert (reason_p.cpu().numpy() == rec["reason"]).all()
     ctx.check()
 
 
-def test_c2_sample_parity(ctx, ocfg):
+@pytest.mark.parametrize("form", ["staged", "fused"])
+def test_c2_sample_parity(ctx, ocfg, form):
     """2,000 frames of the throughput workload's generator (seed 2)."""
     d = gen.workload("c2", n_frames=2000)
     hits, off = _dev(d)
-    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024))
+    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024, form=FORMS[form]))
     s = _check_results(P.compare_batch(ocfg, d["hits"], d["off"], rec))
-    print("c2 sample parity", s)
+    print("c2 sample parity", form, s)
 
 
 def test_c2_full_size_sampled(ctx, ocfg):
@@ -77,6 +82,9 @@ def test_c2_full_size_sampled(ctx, ocfg):
     keep, reason = ctx.select_frames(hits, off)
     ctx.check()
     r = reason.cpu().numpy()
+    # the other forms decide every frame identically
+    for entry in (ctx.select_frames_fused, ctx.select_frames_plain):
+        assert (entry(hits, off)[1].cpu().numpy() == r).all()
     k = keep.cpu().numpy()
     assert ((k == 1) == (r != 0)).all()
     assert r.max() <= 6
@@ -142,13 +150,14 @@ def test_edge_cases(ctx, m3e, cfg, ocfg):
     hits = np.concatenate(frames).astype(np.int32)
     d = dict(hits=hits, off=off)
     assert frames[4].size > 160 and big["hits"].size > cfg["caps"]["max_hits"]
-    rec = _np(ctx.select_frames_debug(*_dev(d), cap_trip=1024, cap_combo=1024))
-    res = P.compare_batch(ocfg, hits, off, rec)
-    _check_results(res, max_boundary_frac=0.5)
-    assert rec["reason"][0] == 0 and rec["reason"][1] == 0 and rec["reason"][2] == 0
-    assert rec["reason"][6] == m3e.HIT_OVERFLOW
-    keep, reason = ctx.select_frames(*_dev(d))
-    assert (reason.cpu().numpy() == rec["reason"]).all()
+    for form in FORMS.values():
+        rec = _np(ctx.select_frames_debug(*_dev(d), cap_trip=1024, cap_combo=1024, form=form))
+        res = P.compare_batch(ocfg, hits, off, rec)
+        _check_results(res, max_boundary_frac=0.5)
+        assert rec["reason"][0] == 0 and rec["reason"][1] == 0 and rec["reason"][2] == 0
+        assert rec["reason"][6] == m3e.HIT_OVERFLOW
+        keep, reason = ctx.select_frames(*_dev(d))
+        assert (reason.cpu().numpy() == rec["reason"]).all()
     ctx.check()
     # an invalid address: frame kept with ERR_BADHIT, EBADHIT latched until checked
     bad = np.concatenate([f0, gen.encode([2], [g["n_ladders"][2]], [0], [0])]).astype(np.int32)
@@ -175,11 +184,12 @@ def test_small_caps_overflow_parity(m3e, cfg):
     oc = O.make_config(c2)
     d = gen.workload("c1", n_frames=400, seed=19)
     with m3e.Context(c2, 0) as ctx:
-        rec = _np(ctx.select_frames_debug(*_dev(d), cap_trip=64, cap_combo=64))
-    res = P.compare_batch(oc, d["hits"], d["off"], rec)
-    _check_results(res)
-    counts = np.bincount(rec["reason"], minlength=7)
-    assert counts[2] > 0 and counts[3] > 0 and counts[4] > 0, counts
+        for form in FORMS.values():
+            rec = _np(ctx.select_frames_debug(*_dev(d), cap_trip=64, cap_combo=64, form=form))
+            res = P.compare_batch(oc, d["hits"], d["off"], rec)
+            _check_results(res)
+            counts = np.bincount(rec["reason"], minlength=7)
+            assert counts[2] > 0 and counts[3] > 0 and counts[4] > 0, counts
 
 
 def test_host_entry_matches_device(ctx):
@@ -196,10 +206,12 @@ def test_host_entry_matches_device(ctx):
     assert (hk.numpy() == keep.cpu().numpy()).all()
 
 
-def test_stats_counters(ctx, m3e, ocfg):
+@pytest.mark.parametrize("form", ["staged", "fused"])
+def test_stats_counters(ctx, m3e, ocfg, form):
     d = gen.workload("c1", n_frames=500, seed=13)
     st = m3e.new_stats()
-    keep, reason = ctx.select_frames(*_dev(d), stats=st)
+    entry = ctx.select_frames if form == "staged" else ctx.select_frames_fused
+    keep, reason = entry(*_dev(d), stats=st)
     torch.cuda.synchronize()
     s = m3e.stats_dict(st)
     assert sum(s["reasons"]) == 500
