@@ -193,6 +193,25 @@ int m3e_set_profiling(m3e_ctx* ctx, int on);
 int m3e_kernel_times(m3e_ctx* ctx, float* main_ms, float* deferred_ms);
 int m3e_stage_times(m3e_ctx* ctx, float* ms, int n);
 
+/* Selection without any device allocation in the call (the paper has no
+ * counterpart; this is a deployment aid).  Same decisions as m3e_select_frames,
+ * through the fused kernels, with their scratch in a fixed static device array
+ * instead of context memory that grows with the batch.  For callers that must
+ * not allocate once running: a filter loop at a fixed frame rate cannot take the
+ * device synchronisation of cudaMalloc/cudaFree, and a process sharing the GPU
+ * under a fixed memory budget reserves all memory at start-up.  The context must
+ * exist already (m3e_create allocates; create it during initialisation).
+ *   - At most 262,144 frames per call; more returns M3E_EINVAL.
+ *   - The first call on a device looks up the array's device address (set-up);
+ *     make that first call before any stream capture.
+ *   - The array is shared by all calls on a device and keeps the last call's
+ *     contents; the call clears what must start at zero.  Calls that overlap on
+ *     the GPU (other streams, other contexts of the same device, other threads)
+ *     race on it: serialise them.
+ *   - No statistics or candidate record. */
+int m3e_select_frames_noalloc(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                              uint8_t* d_keep, uint8_t* d_reason, cudaStream_t stream);
+
 const char* m3e_last_error_string(void);
 int m3e_version(void);
 

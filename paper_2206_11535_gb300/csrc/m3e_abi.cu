@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -622,3 +623,77 @@ int m3e_select_frames_host(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_o
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ selection without allocation
+//
+// m3e_select_frames_noalloc runs the fused kernels with their scratch (work-queue
+// head, deferred-frame count, deferred-frame list) in the static device array
+// below instead of context memory that grows with the batch.  It exists for
+// callers that must not allocate device memory once they are running: a filter
+// process that reads out frames at a fixed rate cannot afford the implicit device
+// synchronisation and the milliseconds of a cudaMalloc/cudaFree in its loop, and
+// a process that shares the GPU under a fixed memory budget reserves everything at
+// start-up.  The price is a fixed upper bound on the frames of one call.
+
+namespace {
+
+constexpr int64_t NOALLOC_MAX_FRAMES = 1 << 18;  // frames per call (1 MB of scratch)
+constexpr int NOALLOC_HEAD = 4;                  // [0] queue head, [1] deferred count, [2..3] unused
+
+// Shared by every call on a device, holding the last call's contents; calls that
+// overlap on the GPU race on it.
+static __device__ __align__(256) int g_noalloc_scratch[NOALLOC_HEAD + NOALLOC_MAX_FRAMES];
+
+std::mutex g_noalloc_mu;
+int* g_noalloc_ptr[256] = {};  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on `dev` (current device), looked up once.
+int noalloc_scratch(int dev, int** out) {
+  if (dev < 0 || dev >= 256) return fail(M3E_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(M3E_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<int*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return M3E_OK;
+}
+
+}  // namespace
+
+extern "C" int m3e_select_frames_noalloc(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_frame_off,
+                                         int64_t n_frames, uint8_t* d_keep, uint8_t* d_reason, cudaStream_t s) {
+  if (!x) return fail(M3E_EINVAL, "ctx is NULL");
+  if (n_frames > NOALLOC_MAX_FRAMES)
+    return fail(M3E_EINVAL, "m3e_select_frames_noalloc takes at most %lld frames per call, got %lld",
+                (long long)NOALLOC_MAX_FRAMES, (long long)n_frames);
+  int rc = check_batch(d_hits, d_frame_off, n_frames, d_keep, d_reason);
+  if (rc) return rc;
+  x->last_launches = 0;
+  x->prof_valid = false;
+  if (n_frames == 0) return M3E_OK;
+  DeviceGuard guard(x->device);
+  int* scratch = nullptr;
+  rc = noalloc_scratch(x->device, &scratch);
+  if (rc) return rc;
+  KParams p{};
+  p.col_lut = x->col_lut;
+  p.row_lut = x->row_lut;
+  p.err = x->err;
+  p.work = scratch;
+  p.defer_list = scratch + NOALLOC_HEAD;
+  p.grab = x->grab;
+  p.hits = d_hits;
+  p.off = d_frame_off;
+  p.n_frames = n_frames;
+  p.keep = d_keep;
+  p.reason = d_reason;
+  // the queue head and the deferred count start at zero; the list is written before it is read
+  CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * sizeof(int), s));
+  CUDA_TRY(launch_fused(x->dc, p, x->sms * x->fused_bpsm, false, s));
+  CUDA_TRY(launch_deferred(x->dc, p, 2 * x->sms, false, s));
+  x->last_launches = 2;
+  return M3E_OK;
+}

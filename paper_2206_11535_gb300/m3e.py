@@ -68,6 +68,7 @@ def _load(path: str = LIB_PATH):
     lib.m3e_select_frames_debug.argtypes = [vp, C.c_int, vp, vp, i64, vp, vp, C.POINTER(Dump), vp]
     lib.m3e_stage_times.argtypes = [vp, C.POINTER(C.c_float), C.c_int]
     lib.m3e_select_frames_host.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    lib.m3e_select_frames_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.m3e_check.argtypes = [vp, vp]
     lib.m3e_set_launch.argtypes = [vp, C.c_int, C.c_int]
     lib.m3e_last_launch_count.argtypes = [vp]
@@ -210,6 +211,16 @@ class Context:
                                            C.byref(d), _stream(stream)))
         rec["keep"], rec["reason"] = keep, reason
         return rec
+
+    def select_frames_noalloc(self, hits, off, keep, reason, stream=None):
+        """``m3e_select_frames_noalloc``: the selection without any device allocation in
+        the call, for callers that must not allocate while running (fixed-rate
+        loops, fixed memory budgets).  ``keep`` and ``reason`` must be allocated by
+        the caller beforehand; at most 262,144 frames per call."""
+        nf = off.numel() - 1
+        _check(lib.m3e_select_frames_noalloc(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
+                                             _stream(stream)))
+        return keep, reason
 
     def select_frames_host(self, hits: np.ndarray, off: np.ndarray, keep=None, reason=None, stream=None):
         """``m3e_select_frames_host`` on host arrays (numpy or pinned torch CPU tensors).
