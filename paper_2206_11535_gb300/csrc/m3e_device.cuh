@@ -49,7 +49,7 @@ struct TrkSoA {
   int tid[CK];                      // index of the triplet it came from
 };
 
-template <int CH, int CT, int CK, int CC>
+template <int CH, int CT, int CK, int CC, int CH32 = (CH <= W_HITS ? CH : 1)>
 struct FrameSm {
   float x[CH], y[CH], z[CH], phi[CH];
   uint32_t addr[CH];
@@ -57,6 +57,12 @@ struct FrameSm {
   uint8_t bin[CH];
   uint16_t bstart[NBK + 1];
   int bcur[NBK];
+  // warp stage, selection cuts: Phi01 / Phi12 partners of the layer-1 hits (regions
+  // r01 / r12, counts c12) and the start of each layer-1 hit's candidate triplets
+  uint8_t p01[CH32 == 1 ? 1 : W_P01], p12[CH32 == 1 ? 1 : W_P12];
+  uint16_t r01[CH32], r12[CH32];
+  uint8_t c12[CH32];
+  int cst[CH32 + 1];
   TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
     ushort4 trip[CT];           // selected triplets (sorted-hit indices)
@@ -677,42 +683,165 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
   }
   g.sync();
 
-  // ---- C: selection cuts (Algorithm 2), pairs restricted to reachable phi bins
+  // ---- C: selection cuts (Algorithm 2), pairs restricted to reachable phi bins.
+  // The bins of a window are contiguous in the sorted order, so a window is one
+  // index range, or two when it wraps past phi = 2 pi.
   {
     unsigned npair = 0, ntt = 0;
     const int l1a = sm.bstart[NB], l1b = sm.bstart[2 * NB];
     const int nb0 = min(2 * C.k01 + 1, NB), nb2 = min(2 * C.k12 + 1, NB);
-    for (int i1 = l1a + g.rank(); i1 < l1b; i1 += G::N) {
-      const float x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
-      const int b1 = sm.bin[i1];
-      const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
-      const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
-      for (int w0 = 0; w0 < nb0; ++w0) {
-        const int bb0 = (s0 + w0) & (NB - 1);
-        const int e0 = sm.bstart[bb0 + 1];
-        for (int i0 = sm.bstart[bb0]; i0 < e0; ++i0) {
-          const float x0 = sm.x[i0], y0 = sm.y[i0];
-          ++npair;
-          if (!(x0 * x1 + y0 * y1 >= C.c01)) continue;
-          const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
-          for (int w2 = 0; w2 < nb2; ++w2) {
-            const int bb2 = 2 * NB + ((s2 + w2) & (NB - 1));
-            const int e2 = sm.bstart[bb2 + 1];
-            for (int i2 = sm.bstart[bb2]; i2 < e2; ++i2) {
-              const float x2 = sm.x[i2], y2 = sm.y[i2];
-              ++npair;
-              if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
-              ++ntt;
-              const float dl = (sm.z[i2] - z1) * C.inv_dr12 - tl01;
-              if (!(fabsf(dl) <= C.dl_max)) continue;
+    if constexpr (G::N == 32) {
+      // Warp: the work is flattened so that every lane has a candidate at every
+      // step.  A: one lane per layer-1 hit collects its Phi01 and Phi12 partners
+      // into regions reserved by a prefix sum of the window sizes.  B: a prefix sum
+      // of the products c01 * c12 numbers the candidate triplets of all layer-1
+      // hits.  C: the lanes share that flat list (a binary search finds the
+      // layer-1 hit of a candidate) for the Delta lambda and r_tc tests.
+      const int lane = g.rank();
+      const int n1 = l1b - l1a;
+      int base0 = 0, base2 = 0, basec = 0;
+      bool over = false;
+      for (int j0 = 0; j0 < n1; j0 += 32) {
+        const int j = j0 + lane;
+        const int i1 = l1a + j;
+        int n0w = 0, n2w = 0, a0 = 0, n0a = 0, a2 = 0, n2a = 0;
+        float x1 = 0.f, y1 = 0.f;
+        if (j < n1) {
+          x1 = sm.x[i1];
+          y1 = sm.y[i1];
+          const int b1 = sm.bin[i1];
+          const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
+          const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
+          a0 = sm.bstart[s0];
+          n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
+          n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
+          a2 = sm.bstart[2 * NB + s2];
+          n2a = sm.bstart[2 * NB + min(s2 + nb2, NB)] - a2;
+          n2w = n2a + (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - sm.bstart[2 * NB] : 0);
+        }
+        npair += n0w + n2w;
+        // exclusive prefix of the window sizes: each layer-1 hit's region of partners
+        int e0 = n0w, e2 = n2w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t0 = __shfl_up_sync(FULL, e0, o), t2 = __shfl_up_sync(FULL, e2, o);
+          if (lane >= o) {
+            e0 += t0;
+            e2 += t2;
+          }
+        }
+        const int r0 = base0 + e0 - n0w, r2 = base2 + e2 - n2w;
+        base0 += __shfl_sync(FULL, e0, 31);
+        base2 += __shfl_sync(FULL, e2, 31);
+        over = over || base0 > W_P01 || base2 > W_P12;
+        int c01 = 0, c12 = 0;
+        if (j < n1 && !over) {
+          for (int k = 0; k < n0w; ++k) {
+            const int i0 = k < n0a ? a0 + k : k - n0a;
+            if (sm.x[i0] * x1 + sm.y[i0] * y1 >= C.c01) sm.p01[r0 + c01++] = (uint8_t)i0;
+          }
+          if (c01)
+            for (int k = 0; k < n2w; ++k) {
+              const int i2 = k < n2a ? a2 + k : sm.bstart[2 * NB] + (k - n2a);
+              if (x1 * sm.x[i2] + y1 * sm.y[i2] >= C.c12) sm.p12[r2 + c12++] = (uint8_t)i2;
+            }
+          sm.r01[j] = (uint16_t)r0;
+          sm.r12[j] = (uint16_t)r2;
+          sm.c12[j] = (uint8_t)c12;
+        }
+        // B: exclusive prefix of the candidate-triplet counts
+        const int nc = c01 * c12;
+        ntt += nc;
+        int ec = nc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(FULL, ec, o);
+          if (lane >= o) ec += t;
+        }
+        if (j < n1) sm.cst[j] = basec + ec - nc;
+        basec += __shfl_sync(FULL, ec, 31);
+      }
+      if (lane == 0) sm.cst[n1] = basec;
+      sm.bad = __any_sync(FULL, over) ? 2 : 0;
+      __syncwarp();
+      if (sm.bad == 2) {
+        ntt = 0;
+        if (lane != 0) npair = 0;
+      } else {
+        // C: the flat list of candidate triplets
+        int nt = 0;
+        const int T = basec;
+        for (int k0 = 0; k0 < T; k0 += 32) {
+          const int k = k0 + lane;
+          bool pass = false;
+          int i0 = 0, i1 = 0, i2 = 0;
+          if (k < T) {
+            int lo = 0, hi = n1;  // last j with cst[j] <= k
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (sm.cst[mid] <= k) lo = mid; else hi = mid;
+            }
+            const int j = lo;
+            const int u = k - sm.cst[j];
+            const int cq = sm.c12[j];
+            const int qa = u / cq;
+            i1 = l1a + j;
+            i0 = sm.p01[sm.r01[j] + qa];
+            i2 = sm.p12[sm.r12[j] + (u - qa * cq)];
+            const float x0 = sm.x[i0], y0 = sm.y[i0], x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
+            const float x2 = sm.x[i2], y2 = sm.y[i2];
+            const float dl = (sm.z[i2] - z1) * C.inv_dr12 - (z1 - sm.z[i0]) * C.inv_dr01;
+            if (fabsf(dl) <= C.dl_max) {
               const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
               const float cr = ax * by - ay * bx;
               const float ex = x2 - x0, ey = y2 - y0;
               const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
               const float Qq = cr * cr;
-              if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
-              const int k = atomicAdd(&sm.ntrip, 1);
-              if (k < CT) sm.u.trip[k] = make_ushort4((uint16_t)i0, (uint16_t)i1, (uint16_t)i2, 0);
+              pass = cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq;
+            }
+          }
+          const unsigned m = __ballot_sync(FULL, pass);
+          const int kk = nt + __popc(m & ((1u << lane) - 1u));
+          if (pass && kk < CT) sm.u.trip[kk] = make_ushort4((uint16_t)i0, (uint16_t)i1, (uint16_t)i2, 0);
+          nt += __popc(m);
+        }
+        if (lane == 0) sm.ntrip = nt;
+        if (lane != 0) npair = ntt = 0;  // counted once per warp
+      }
+    } else {
+      for (int i1 = l1a + g.rank(); i1 < l1b; i1 += G::N) {
+        const float x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
+        const int b1 = sm.bin[i1];
+        const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
+        const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
+        const int r0[4] = {sm.bstart[s0], sm.bstart[min(s0 + nb0, NB)], sm.bstart[0],
+                           s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : sm.bstart[0]};
+        const int r2[4] = {sm.bstart[2 * NB + s2], sm.bstart[2 * NB + min(s2 + nb2, NB)], sm.bstart[2 * NB],
+                           s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] : sm.bstart[2 * NB]};
+        npair += (r0[1] - r0[0]) + (r0[3] - r0[2]) + (r2[1] - r2[0]) + (r2[3] - r2[2]);
+#pragma unroll
+        for (int q0 = 0; q0 < 2; ++q0) {
+          for (int i0 = r0[2 * q0]; i0 < r0[2 * q0 + 1]; ++i0) {
+            const float x0 = sm.x[i0], y0 = sm.y[i0];
+            if (!(x0 * x1 + y0 * y1 >= C.c01)) continue;
+            const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
+#pragma unroll
+            for (int q2 = 0; q2 < 2; ++q2) {
+              for (int i2 = r2[2 * q2]; i2 < r2[2 * q2 + 1]; ++i2) {
+                const float x2 = sm.x[i2], y2 = sm.y[i2];
+                if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
+                ++ntt;
+                const float dl = (sm.z[i2] - z1) * C.inv_dr12 - tl01;
+                if (!(fabsf(dl) <= C.dl_max)) continue;
+                const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
+                const float cr = ax * by - ay * bx;
+                const float ex = x2 - x0, ey = y2 - y0;
+                const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
+                const float Qq = cr * cr;
+                if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
+                const int k = atomicAdd(&sm.ntrip, 1);
+                if (k < CT) sm.u.trip[k] = make_ushort4((uint16_t)i0, (uint16_t)i1, (uint16_t)i2, 0);
+              }
             }
           }
         }
@@ -724,6 +853,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     }
   }
   g.sync();
+  if (DEFER && sm.bad == 2) return DEFERRED;  // partner lists beyond the warp stage's capacity
   const int ntrip = sm.ntrip;
   if (DEBUG && g.leader()) P.dump.n_trip[f] = ntrip;
   if (ntrip > C.max_trip) return M3E_TRIPLET_OVERFLOW;
