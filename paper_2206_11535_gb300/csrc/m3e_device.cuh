@@ -458,12 +458,9 @@ struct VtxOut {
   float chi2, tdist, ptot;
 };
 
-// Intersection points of the circles of tracks a and b, in two fixed slots (q0
-// first, as the oracle orders them), each with the target-filter flag and the
-// error sum of both tracks.  Returns 0 when the circles do not intersect.
 // Whether the transverse circles (centre, radius) of two tracks intersect, with
 // the distance D of the centres, the foot aa of the chord on the centre line and
-// the squared half chord h2 (one routine for the prefilter and the vertex).
+// the squared half chord h2.
 __device__ __forceinline__ bool circles_meet(float acx, float acy, float ar, float bcx, float bcy, float br, float& D,
                                              float& aa, float& h2) {
   const float ex = bcx - acx, ey = bcy - acy;
@@ -474,23 +471,44 @@ __device__ __forceinline__ bool circles_meet(float acx, float acy, float ar, flo
   return !(h2 < 0.f);
 }
 
-__device__ __forceinline__ int pair_points(const TrackR& a, const TrackR& b, const DevCfg& C, float& x0, float& y0,
-                                           float& v0, bool& k0, float& x1, float& y1, float& v1, bool& k1) {
+// Intersection points of the circles of tracks a and b, in two fixed slots (q0
+// first, as the oracle orders them), each with its target-filter flag.  Returns
+// false when the circles do not intersect.  One routine for the prefilter of the
+// vertex stage and for the vertex itself, so both take the same decisions.
+__device__ __forceinline__ bool pair_geometry(float acx, float acy, float ar, float bcx, float bcy, float br,
+                                              float lim, float& x0, float& y0, bool& k0, float& x1, float& y1,
+                                              bool& k1) {
   k0 = k1 = false;
-  v0 = v1 = 1.f;
   float D, aa, h2;
-  if (!circles_meet(a.cx, a.cy, a.rt, b.cx, b.cy, b.rt, D, aa, h2)) return 0;
-  float ex = b.cx - a.cx, ey = b.cy - a.cy;
-  ex /= D;
-  ey /= D;
-  const float bx = a.cx + aa * ex, by = a.cy + aa * ey;
+  if (!circles_meet(acx, acy, ar, bcx, bcy, br, D, aa, h2)) return false;
+  const float ex = (bcx - acx) / D, ey = (bcy - acy) / D;
+  const float bx = acx + aa * ex, by = acy + aa * ey;
   const float h = sqrtf(h2);
   x0 = bx - h * ey;
   y0 = by + h * ex;
   x1 = bx + h * ey;
   y1 = by - h * ex;
-  k0 = sqrtf(x0 * x0 + y0 * y0) <= C.isect_lim;
-  k1 = h2 != 0.f && sqrtf(x1 * x1 + y1 * y1) <= C.isect_lim;
+  k0 = sqrtf(x0 * x0 + y0 * y0) <= lim;
+  k1 = h2 != 0.f && sqrtf(x1 * x1 + y1 * y1) <= lim;
+  return true;
+}
+
+// Status of a combination after the first two vertex steps: 0 a pair of circles
+// does not intersect, 1 the target filter leaves a pair without points, 2 go on.
+__device__ __forceinline__ int vertex_prefilter(const float* a, const float* b, const float* e, float lim) {
+  float x0, y0, x1, y1;
+  bool k0, k1, k2, k3, k4, k5;
+  if (!pair_geometry(a[0], a[1], a[2], b[0], b[1], b[2], lim, x0, y0, k0, x1, y1, k1)) return 0;
+  if (!pair_geometry(a[0], a[1], a[2], e[0], e[1], e[2], lim, x0, y0, k2, x1, y1, k3)) return 0;
+  if (!pair_geometry(b[0], b[1], b[2], e[0], e[1], e[2], lim, x0, y0, k4, x1, y1, k5)) return 0;
+  return (k0 || k1) && (k2 || k3) && (k4 || k5) ? 2 : 1;
+}
+
+// pair_geometry plus the error of each surviving point (sum of both tracks' errors).
+__device__ __forceinline__ int pair_points(const TrackR& a, const TrackR& b, const DevCfg& C, float& x0, float& y0,
+                                           float& v0, bool& k0, float& x1, float& y1, float& v1, bool& k1) {
+  v0 = v1 = 1.f;
+  if (!pair_geometry(a.cx, a.cy, a.rt, b.cx, b.cy, b.rt, C.isect_lim, x0, y0, k0, x1, y1, k1)) return 0;
   if (k0) v0 = point_var(a, x0, y0, C.sig_pix2) + point_var(b, x0, y0, C.sig_pix2);
   if (k1) v1 = point_var(a, x1, y1, C.sig_pix2) + point_var(b, x1, y1, C.sig_pix2);
   return 1;
@@ -533,10 +551,19 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
   if (!(k00 || k01) || !(k10 || k11) || !(k20 || k21)) return o;
   float best = FLT_MAX, bmx = 0.f, bmy = 0.f, bmz = 0.f;
   bool have = false;
-#pragma unroll 1
+  // the valid choices as a bit set, visited in increasing order (s2 fastest, as the
+  // oracle's loops), so each lane runs only its own choices
+  unsigned valid = 0;
+#pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const bool s0 = (c >> 2) & 1, s1 = (c >> 1) & 1, s2 = c & 1;  // s2 fastest, as the oracle's loops
-    if (!(s0 ? k01 : k00) || !(s1 ? k11 : k10) || !(s2 ? k21 : k20)) continue;
+    const bool s0 = (c >> 2) & 1, s1 = (c >> 1) & 1, s2 = c & 1;
+    if ((s0 ? k01 : k00) && (s1 ? k11 : k10) && (s2 ? k21 : k20)) valid |= 1u << c;
+  }
+#pragma unroll 1
+  while (valid) {
+    const int c = __ffs(valid) - 1;
+    valid &= valid - 1;
+    const bool s0 = (c >> 2) & 1, s1 = (c >> 1) & 1, s2 = c & 1;
     const float w0 = 1.f / (s0 ? v01 : v00), w1 = 1.f / (s1 ? v11 : v10), w2 = 1.f / (s2 ? v21 : v20);
     const float iws = 1.f / (w0 + w1 + w2);
     const float mx = ((s0 ? x01 : x00) * w0 + (s1 ? x11 : x10) * w1 + (s2 ? x21 : x20) * w2) * iws;

@@ -284,11 +284,11 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
 }
 
 // ---- stage 4: vertex of every combination, compacted per warp
-// About three quarters of the combinations fail at the first step (a pair of
-// track circles that does not intersect).  Each warp therefore tests 32
-// combinations at a time for that, appends the survivors to a queue in shared
-// memory, and runs the full vertex on 32 queued survivors at a time, so that all
-// lanes do the expensive part together.
+// Most combinations stop at the first two steps (a pair of track circles that
+// does not intersect, or no intersection inside the target filter).  Each warp
+// therefore runs those steps on 32 combinations at a time, appends the survivors
+// to a queue in shared memory, and runs the full vertex on 32 queued survivors at
+// a time, so that all lanes do the expensive part together.
 constexpr int S4_WARPS = 4;
 
 __device__ __forceinline__ void load_circle(const float4* __restrict__ rec, int64_t k, float& cx, float& cy,
@@ -337,15 +337,15 @@ __global__ void __launch_bounds__(S4_WARPS * 32)
         const int4 r = S.combo[i];
         const int f = r.x;
         if (f >= 0 && S.fstate[f] == PENDING && (DEBUG || !*((volatile int*)S.ffound + f))) {
-          float ax, ay, ar, bx, by, br, ex, ey, er, D, aa, h2;
-          load_circle(S.trec, r.y, ax, ay, ar);
-          load_circle(S.trec, r.z, bx, by, br);
-          load_circle(S.trec, r.w, ex, ey, er);
-          cand = circles_meet(ax, ay, ar, bx, by, br, D, aa, h2) && circles_meet(ax, ay, ar, ex, ey, er, D, aa, h2) &&
-                 circles_meet(bx, by, br, ex, ey, er, D, aa, h2);
-          if (DEBUG && !cand) {  // record the combination with status 0 (no intersection)
+          float ca[3], cb[3], ce[3];
+          load_circle(S.trec, r.y, ca[0], ca[1], ca[2]);
+          load_circle(S.trec, r.z, cb[0], cb[1], cb[2]);
+          load_circle(S.trec, r.w, ce[0], ce[1], ce[2]);
+          const int st = vertex_prefilter(ca, cb, ce, C.isect_lim);
+          cand = st == 2;
+          if (DEBUG && !cand) {  // record the combination with its early status
             VtxOut v;
-            v.status = 0;
+            v.status = st;
             v.pass = 0;
             v.chi2 = v.tdist = v.ptot = FLT_MAX;
             const float4 qa = __ldg(S.trec + 4 * (int64_t)r.y + 1), qb = __ldg(S.trec + 4 * (int64_t)r.z + 1),
