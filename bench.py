@@ -35,24 +35,25 @@ WORKLOAD = ("full-rate throughput: 1,000,000 frames per GPU, Poisson(20) tracks/
 # Arithmetic operations per work item of the method's formulas (FMA = 2, each
 # transcendental, division or square root = 1), grouped by the stage kernel that
 # does the work; see DESIGN.md "Roofline".
-STAGE_OPS = {
-    "stage1 decode+sort+cuts": {"pair_tests": 4, "triplet_tests": 6},
-    "stage2 track fits": {"triplets": 460},
-    "stage3 energy test": {"energy_tests": 7},
-    "stage4 vertex": {"combos": 75, "vertexed": 565},
-    "stage5 decision": {},
+STAGE_OPS = {  # name: (indices into m3e_stage_times, ops per counted item)
+    "stage1 decode+sort+cuts (warp and CTA tiers)": ((0, 1, 2), {"pair_tests": 4, "triplet_tests": 6}),
+    "stage2 track fits": ((3,), {"triplets": 460}),
+    "stage3 energy test": ((4,), {"energy_tests": 7}),
+    "stage4 vertex": ((5,), {"combos": 75, "vertexed": 565}),
+    "stage5 decision": ((6,), {}),
 }
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
     return ap.parse_args()
 
 
@@ -80,7 +81,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -251,12 +252,14 @@ def main():
             ms = float(t.item())
         return ms, ks
 
-    # main arm: the staged form, kernel durations recorded on the launching stream
-    ctx.set_profiling(True)
+    # main arm: the staged form, back to back, SM clocks sampled during the timed region
     with Clocks(local) as clk:
-        ms, ks = timed(lambda: ctx.select_frames(hits, off, keep, reason, stream=stream), args.steps,
-                       args.warmup, profile=True)
+        ms, _ = timed(lambda: ctx.select_frames(hits, off, keep, reason, stream=stream), args.steps, args.warmup)
     launches = ctx.last_launch_count() * args.steps
+    # kernel durations, from CUDA events recorded by the library on the launching stream
+    ctx.set_profiling(True)
+    _, ks = timed(lambda: ctx.select_frames(hits, off, keep, reason, stream=stream), max(3, args.steps // 4), 1,
+                  profile=True)
     ctx.set_profiling(False)
     # the fused (one persistent kernel, warp per frame) and plain (CTA per frame) forms
     alt_steps = max(2, args.steps // 2)
@@ -273,23 +276,48 @@ def main():
         e2e = {"value": world * nf * args.steps / (ms_e2e / 1e3), "unit": "frames/s",
                "h2d_bytes_per_step": int(hh.numel() * 4 + ho.numel() * 8), "d2h_bytes_per_step": int(2 * nf),
                "ms_per_step": ms_e2e / args.steps}
+    # uneven frames (lognormal track counts, 1 % of frames at 100x noise): staged vs plain
+    c3 = None
+    if not args.no_c3:
+        dc = gen.workload("c3", seed=3 + 7919 * rank)
+        h3 = torch.from_numpy(dc["hits"]).to(dev)
+        o3 = torch.from_numpy(dc["off"]).to(dev)
+        n3 = dc["off"].size - 1
+        k3 = torch.empty(n3, dtype=torch.uint8, device=dev)
+        r3 = torch.empty(n3, dtype=torch.uint8, device=dev)
+        ms3, _ = timed(lambda: ctx.select_frames(h3, o3, k3, r3, stream=stream), args.steps, args.warmup)
+        rs = r3.clone()
+        ctx.set_profiling(True)
+        _, k3s = timed(lambda: ctx.select_frames(h3, o3, k3, r3, stream=stream), 3, 1, profile=True)
+        ctx.set_profiling(False)
+        ms3p, _ = timed(lambda: ctx.select_frames_plain(h3, o3, k3, r3, stream=stream), alt_steps, 1)
+        c3 = {"workload": "200,000 frames, tracks min(400, lognormal(median 15, sigma 1)), 0.5 noise/layer, "
+                          "1% of frames at 100x noise, seed 3",
+              "staged_frames_per_s": world * n3 * args.steps / (ms3 / 1e3),
+              "plain_frames_per_s": world * n3 * alt_steps / (ms3p / 1e3),
+              "speedup_of_staged": (ms3p / alt_steps) / (ms3 / args.steps),
+              "identical_decisions": bool(torch.equal(rs, r3)),
+              "stage_ms": [round(float(x), 3) for x in np.mean(np.array(k3s), axis=0)],
+              "frames_over_160_hits": int((np.diff(dc["off"]) > 160).sum())}
+        del h3, o3
     # the main arm's decisions are those of the last timed staged call
     ctx.select_frames(hits, off, keep, reason, stream=stream)
     ctx.check()
 
     value = world * nf * args.steps / (ms / 1e3)
-    st_ms = np.mean(np.array(ks), axis=0) if ks else np.full(6, np.nan)
+    st_ms = np.mean(np.array(ks), axis=0) if ks else np.full(8, np.nan)
     props = torch.cuda.get_device_properties(dev)
     cl = clk.summary()
     f_mhz = cl["sm_mhz"] or 1455.0
     peak = props.multi_processor_count * 128 * 2 * f_mhz * 1e6 / 1e12
     stages = []
-    for i, (name, per) in enumerate(STAGE_OPS.items()):
+    for name, (idx, per) in STAGE_OPS.items():
         ops = sum(stats[k] * v for k, v in per.items())
-        t = float(st_ms[i])
+        t = float(sum(st_ms[i] for i in idx))
         stages.append({"kernel": name, "ms": t, "ops": ops, "tflops": ops / (t / 1e3) / 1e12 if t > 0 else 0.0,
                        "frac_of_peak": ops / (t / 1e3) / 1e12 / peak if t > 0 else 0.0})
-    stages.append({"kernel": "deferred frames (CTA per frame)", "ms": float(st_ms[5])})
+    stages.append({"kernel": "deferred frames (CTA per frame)", "ms": float(st_ms[7])})
+    stages[0]["ms_tiers"] = [float(st_ms[0]), float(st_ms[1]), float(st_ms[2])]
     dom = max(stages[:5], key=lambda x: x["ms"])
     tr = recorded_traffic(nf)
     roof = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
@@ -313,6 +341,7 @@ def main():
                                "speedup_of_staged": (ms_plain / alt_steps) / (ms / args.steps)},
            "kept_fraction": float(keep.float().mean().item()),
            "reasons": dict(zip(m3e.REASONS, stats["reasons"][:7])),
+           "uneven_frames_c3": c3,
            "roofline": roof, "e2e": e2e, "clocks": cl, "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(d)

@@ -99,7 +99,8 @@ typedef struct {
   unsigned long long frames, hits;
   unsigned long long pair_tests;     /* Phi tests of layer-0/1 and layer-1/2 hit pairs */
   unsigned long long triplet_tests;  /* Delta-lambda tests after both Phi cuts */
-  unsigned long long triplets;       /* selected triplets (fits run) */
+  unsigned long long triplets;       /* selected triplets of frames that do not overflow (fits run);
+                                        the cuts of an overflowing frame stop once it overflows */
   unsigned long long tracks;         /* tracks kept by the chi2 cut */
   unsigned long long energy_tests;   /* e+ e+ e- combinations tested for energy */
   unsigned long long combos;         /* combinations passing the energy test */
@@ -187,8 +188,10 @@ int m3e_last_launch_count(const m3e_ctx* ctx);
  * m3e_kernel_times waits for the events of the last call and returns the
  * duration in ms of the main kernels (the five staged kernels, the fused kernel
  * or the plain kernel) and of the deferred-frame kernel (0 for the plain form).
- * m3e_stage_times returns up to 6 durations of the last staged call: stages 1-5
- * and the deferred-frame kernel.  Timing adds no device sync. */
+ * m3e_stage_times returns up to 8 durations of the last staged call: stage 1
+ * (warp tier), stage 1 (middle and top CTA tiers), stages 2-5 and the
+ * deferred-frame kernel.
+ * Timing adds no device sync. */
 int m3e_set_profiling(m3e_ctx* ctx, int on);
 int m3e_kernel_times(m3e_ctx* ctx, float* main_ms, float* deferred_ms);
 int m3e_stage_times(m3e_ctx* ctx, float* ms, int n);

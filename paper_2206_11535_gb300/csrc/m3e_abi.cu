@@ -52,9 +52,11 @@ constexpr int HOST_CHUNKS = 8;  // chunks of the host entry point (double-buffer
 // global candidate arrays of the staged form.  The context holds one set for the
 // device entry points and two for the double-buffered host entry point.
 struct Scratch {
-  int* work = nullptr;                      // [0] work-queue head, [1] deferred count
-  unsigned long long* counters = nullptr;   // staged: [0] triplets, [1] combinations, [2] stage-3 queue
-  int* defer = nullptr;
+  int* work = nullptr;                      // [0] work-queue head, [1] list-1 count, [2] list-2 count
+  unsigned long long* counters = nullptr;   // staged: [0] triplets, [1] combinations, [2] stage-3 queue, [3] hits
+  int* defer = nullptr;                     // list 1: deferred frames
+  int* defer2 = nullptr;                    // list 2 (staged form)
+  int* defer1b = nullptr;                   // list 1b (staged form)
   int64_t defer_cap = 0;
   float* hf = nullptr;                      // hx, hy, hz, hphi
   uint32_t* haddr = nullptr;
@@ -62,7 +64,7 @@ struct Scratch {
   int64_t hits_cap = 0;
   uint16_t* l3 = nullptr;
   int* fint = nullptr;                      // fstate, ftbase, fntrip, ffound, fncombo
-  long long* fcbase = nullptr;
+  long long* fcbase = nullptr;              // fcbase, fhbase
   int64_t frames_cap = 0;
   int4* trip = nullptr;
   uint8_t* tstatus = nullptr;
@@ -75,8 +77,9 @@ struct Scratch {
 struct m3e_ctx {
   int device = 0;
   int sms = 1;
-  int fused_bpsm = 1, s1_bpsm = 1, s2_bpsm = 1, s3_bpsm = 1, s4_bpsm = 1;
+  int fused_bpsm = 1, s1_bpsm = 1, s2_bpsm = 1, s3_bpsm = 1, s4_bpsm = 1, s1c_bpsm = 1, s1m_bpsm = 1;
   int grab = 4;
+  int defer_hits = W_HITS;
   m3e_config cfg{};
   DevCfg dc{};
   float4* col_lut = nullptr;
@@ -97,7 +100,7 @@ struct m3e_ctx {
   bool prof = false;
   bool prof_valid = false;
   int prof_kind = 0;            // 0 staged, 1 fused, 2 plain
-  cudaEvent_t pe[8] = {};
+  cudaEvent_t pe[10] = {};
 };
 
 namespace {
@@ -197,7 +200,11 @@ KParams base_params(m3e_ctx* x, Scratch& sc) {
   p.work = sc.work;
   p.err = x->err;
   p.defer_list = sc.defer;
+  p.defer_count = sc.work + 1;
+  p.in_list = sc.defer;
+  p.in_count = sc.work + 1;
   p.grab = x->grab;
+  p.defer_hits = x->defer_hits;
   return p;
 }
 
@@ -212,18 +219,31 @@ int grow(T*& ptr, int64_t& cap, int64_t need, size_t elem, const char* what) {
   return M3E_OK;
 }
 
-// Scratch for a batch of nf frames (staged arrays only when staged: each pending
-// frame keeps its sorted hits in a fixed slot of S1_HITS entries).
+// Scratch for a batch of nf frames (staged arrays only when staged; the sorted
+// hits of pending frames take HITS_PER_FRAME entries per frame on average, frames
+// beyond that are deferred to the CTA-per-frame kernel).
+constexpr int64_t HITS_PER_FRAME = 128;
+
 int ensure_scratch(Scratch& sc, int64_t nf, bool staged) {
-  const int64_t nh = nf * S1_HITS;
+  const int64_t nh = nf * HITS_PER_FRAME > (1 << 16) ? nf * HITS_PER_FRAME : (1 << 16);
   int64_t one = sc.work ? 1 : 0;
   int rc = grow(sc.work, one, 1, 4 * sizeof(int), "work counters");
   if (rc) return rc;
   int64_t one2 = sc.counters ? 1 : 0;
   rc = grow(sc.counters, one2, 1, 4 * sizeof(unsigned long long), "counters");
   if (rc) return rc;
-  rc = grow(sc.defer, sc.defer_cap, nf > 4096 ? nf : 4096, sizeof(int), "deferred list");
-  if (rc || !staged) return rc;
+  {
+    const int64_t dc = nf > 4096 ? nf : 4096;
+    if (dc > sc.defer_cap) {
+      int64_t c0 = sc.defer_cap, c1 = sc.defer_cap, c2 = sc.defer_cap;
+      rc = grow(sc.defer, c0, dc, sizeof(int), "deferred list");
+      if (!rc) rc = grow(sc.defer2, c1, dc, sizeof(int), "deferred list 2");
+      if (!rc) rc = grow(sc.defer1b, c2, dc, sizeof(int), "deferred list 1b");
+      if (rc) return rc;
+      sc.defer_cap = dc;
+    }
+  }
+  if (!staged) return M3E_OK;
   int64_t hc = sc.hits_cap;
   if (nh > hc) {
     int64_t c0 = hc, c1 = hc, c2 = hc;
@@ -237,7 +257,7 @@ int ensure_scratch(Scratch& sc, int64_t nf, bool staged) {
     int64_t c0 = sc.frames_cap, c1 = sc.frames_cap, c2 = sc.frames_cap;
     rc = grow(sc.l3, c0, nf, (NB + 1) * sizeof(uint16_t), "layer-3 bins");
     if (!rc) rc = grow(sc.fint, c1, nf, 5 * sizeof(int), "frame state");
-    if (!rc) rc = grow(sc.fcbase, c2, nf, sizeof(long long), "frame combination base");
+    if (!rc) rc = grow(sc.fcbase, c2, nf, 2 * sizeof(long long), "frame combination and hit bases");
     if (rc) return rc;
     sc.frames_cap = nf;
   }
@@ -261,6 +281,8 @@ void free_scratch(Scratch& sc) {
   cudaFree(sc.work);
   cudaFree(sc.counters);
   cudaFree(sc.defer);
+  cudaFree(sc.defer2);
+  cudaFree(sc.defer1b);
   cudaFree(sc.hf);
   cudaFree(sc.haddr);
   cudaFree(sc.hidx);
@@ -290,6 +312,12 @@ SParams staged_params(const Scratch& sc) {
   s.ffound = sc.fint + 3 * F;
   s.fncombo = sc.fint + 4 * F;
   s.fcbase = sc.fcbase;
+  s.fhbase = sc.fcbase + F;
+  s.list1 = sc.defer;
+  s.list2 = sc.defer2;
+  s.list1b = sc.defer1b;
+  s.lcount = sc.work + 1;
+  s.hits_cap = H;
   s.trip = sc.trip;
   s.tstatus = sc.tstatus;
   s.trec = sc.trec;
@@ -320,7 +348,7 @@ int enqueue(m3e_ctx* x, Scratch& sc, KParams p, int form, bool debug, cudaStream
     x->last_launches = 1;
     return M3E_OK;
   }
-  CUDA_TRY(cudaMemsetAsync(sc.work, 0, 2 * sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(sc.work, 0, 4 * sizeof(int), s));  // queue head and the three list counts
   if (form == FORM_FUSED) {
     if (timed) CUDA_TRY(cudaEventRecord(x->pe[0], s));
     CUDA_TRY(launch_fused(x->dc, p, x->sms * x->fused_bpsm, debug, s));
@@ -330,12 +358,17 @@ int enqueue(m3e_ctx* x, Scratch& sc, KParams p, int form, bool debug, cudaStream
     x->last_launches = 2;
     return M3E_OK;
   }
-  CUDA_TRY(cudaMemsetAsync(sc.counters, 0, 3 * sizeof(unsigned long long), s));
-  const int grids[4] = {x->sms * x->s1_bpsm, x->sms * x->s2_bpsm, x->sms * x->s3_bpsm, x->sms * x->s4_bpsm};
-  CUDA_TRY(launch_staged(x->dc, p, staged_params(sc), grids, debug, s, timed ? x->pe : nullptr));
-  CUDA_TRY(launch_deferred(x->dc, p, 2 * x->sms, debug, s));
-  if (timed) CUDA_TRY(cudaEventRecord(x->pe[6], s));
-  x->last_launches = 6;
+  CUDA_TRY(cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), s));
+  const int grids[6] = {x->sms * x->s1_bpsm, x->sms * x->s2_bpsm,  x->sms * x->s3_bpsm,
+                        x->sms * x->s4_bpsm, x->sms * x->s1c_bpsm, x->sms * x->s1m_bpsm};
+  const SParams sp = staged_params(sc);
+  CUDA_TRY(launch_staged(x->dc, p, sp, grids, debug, s, timed ? x->pe : nullptr));
+  KParams pd = p;  // frames no stage could finish: the CTA-per-frame kernel
+  pd.in_list = sp.list2;
+  pd.in_count = sp.lcount + 1;
+  CUDA_TRY(launch_deferred(x->dc, pd, 2 * x->sms, debug, s));
+  if (timed) CUDA_TRY(cudaEventRecord(x->pe[8], s));
+  x->last_launches = 8;
   return M3E_OK;
 }
 
@@ -372,6 +405,8 @@ int m3e_create(const m3e_config* cfg, int cuda_device, m3e_ctx** out) {
   x->s2_bpsm = stage_blocks_per_sm(2);
   x->s3_bpsm = stage_blocks_per_sm(3);
   x->s4_bpsm = stage_blocks_per_sm(4);
+  x->s1c_bpsm = stage_blocks_per_sm(5);
+  x->s1m_bpsm = stage_blocks_per_sm(6);
   // look-up tables in FP64, rounded once
   int ncolt = 0, nrowt = 0;
   for (int L = 0; L < 4; ++L) {
@@ -423,7 +458,7 @@ int m3e_destroy(m3e_ctx* x) {
     if (x->hs[i]) cudaStreamDestroy(x->hs[i]);
     if (x->he[i]) cudaEventDestroy(x->he[i]);
   }
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 10; ++i)
     if (x->pe[i]) cudaEventDestroy(x->pe[i]);
   delete x;
   return M3E_OK;
@@ -445,7 +480,7 @@ int m3e_last_launch_count(const m3e_ctx* x) { return x ? x->last_launches : 0; }
 int m3e_set_profiling(m3e_ctx* x, int on) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
   DeviceGuard guard(x->device);
-  for (int i = 0; i < 8 && on; ++i)
+  for (int i = 0; i < 10 && on; ++i)
     if (!x->pe[i]) CUDA_TRY(cudaEventCreate(&x->pe[i]));
   x->prof = on != 0;
   x->prof_valid = false;
@@ -456,8 +491,8 @@ int m3e_kernel_times(m3e_ctx* x, float* main_ms, float* deferred_ms) {
   if (!x || !main_ms || !deferred_ms) return fail(M3E_EINVAL, "NULL argument");
   if (!x->prof_valid) return fail(M3E_ESTATE, "no timed select call since profiling was enabled");
   DeviceGuard guard(x->device);
-  const int last = x->prof_kind == FORM_STAGED ? 6 : (x->prof_kind == FORM_FUSED ? 2 : 1);
-  const int mid = x->prof_kind == FORM_STAGED ? 5 : 1;
+  const int last = x->prof_kind == FORM_STAGED ? 8 : (x->prof_kind == FORM_FUSED ? 2 : 1);
+  const int mid = x->prof_kind == FORM_STAGED ? 7 : 1;
   CUDA_TRY(cudaEventSynchronize(x->pe[last]));
   CUDA_TRY(cudaEventElapsedTime(main_ms, x->pe[0], x->pe[mid]));
   *deferred_ms = 0.f;
@@ -469,8 +504,8 @@ int m3e_stage_times(m3e_ctx* x, float* ms, int n) {
   if (!x || !ms || n < 1) return fail(M3E_EINVAL, "bad argument");
   if (!x->prof_valid || x->prof_kind != FORM_STAGED) return fail(M3E_ESTATE, "no timed staged select call");
   DeviceGuard guard(x->device);
-  CUDA_TRY(cudaEventSynchronize(x->pe[6]));
-  for (int i = 0; i < n && i < 6; ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], x->pe[i], x->pe[i + 1]));
+  CUDA_TRY(cudaEventSynchronize(x->pe[8]));
+  for (int i = 0; i < n && i < 8; ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], x->pe[i], x->pe[i + 1]));
   return M3E_OK;
 }
 
@@ -684,6 +719,10 @@ extern "C" int m3e_select_frames_noalloc(m3e_ctx* x, const int32_t* d_hits, cons
   p.err = x->err;
   p.work = scratch;
   p.defer_list = scratch + NOALLOC_HEAD;
+  p.defer_count = scratch + 1;
+  p.in_list = scratch + NOALLOC_HEAD;
+  p.in_count = scratch + 1;
+  p.defer_hits = W_HITS;
   p.grab = x->grab;
   p.hits = d_hits;
   p.off = d_frame_off;

@@ -659,7 +659,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     if (g.leader()) atomicOr(P.err, ERR_NEGSIZE);
     return M3E_ERR_BADHIT;
   }
-  if (DEFER && n64 > CH) return DEFERRED;
+  if (DEFER && n64 > (CH < P.defer_hits ? CH : P.defer_hits)) return DEFERRED;
   const int n = (int)(n64 > 0x7fffffff ? 0x7fffffff : n64);
   const int32_t* hp = P.hits + base;
 
@@ -831,12 +831,15 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           const int kk = nt + __popc(m & ((1u << lane) - 1u));
           if (pass && kk < CT) sm.u.trip[kk] = make_ushort4((uint16_t)i0, (uint16_t)i1, (uint16_t)i2, 0);
           nt += __popc(m);
+          if (nt > C.max_trip) break;  // the frame overflows: its decision is known
         }
         if (lane == 0) sm.ntrip = nt;
         if (lane != 0) npair = ntt = 0;  // counted once per warp
       }
     } else {
+      // (a frame whose triplet count passed max_trip overflows whatever follows: stop)
       for (int i1 = l1a + g.rank(); i1 < l1b; i1 += G::N) {
+        if (*(volatile int*)&sm.ntrip > C.max_trip) break;
         const float x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
         const int b1 = sm.bin[i1];
         const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
@@ -851,6 +854,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           for (int i0 = r0[2 * q0]; i0 < r0[2 * q0 + 1]; ++i0) {
             const float x0 = sm.x[i0], y0 = sm.y[i0];
             if (!(x0 * x1 + y0 * y1 >= C.c01)) continue;
+            if (*(volatile int*)&sm.ntrip > C.max_trip) break;
             const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
 #pragma unroll
             for (int q2 = 0; q2 < 2; ++q2) {

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
       if (r == PENDING) r = frame_back<WarpGroup, SmWarp, W_TRIP, W_TRK, W_COMBO, true, DEBUG>(g, sm, C, P, f);
       if (r == DEFERRED) {
         if (g.leader()) {
-          const int k = atomicAdd(&P.work[1], 1);
+          const int k = atomicAdd(P.defer_count, 1);
           P.defer_list[k] = f;
           if (P.stats) sm.acc[ST_DEFER] += 1;
         }
@@ -55,9 +55,9 @@ __global__ void __launch_bounds__(NT) k_select_cta(const __grid_constant__ DevCf
   SmCta& sm = *reinterpret_cast<SmCta*>(smem_raw);
   const CtaGroup<NT> g;
   clear_stats(g, sm);
-  const int count = LIST ? P.work[1] : (int)P.n_frames;
+  const int count = LIST ? *P.in_count : (int)P.n_frames;
   for (int i = blockIdx.x; i < count; i += gridDim.x) {
-    const int f = LIST ? P.defer_list[i] : i;
+    const int f = LIST ? P.in_list[i] : i;
     int r = frame_front<CtaGroup<NT>, SmCta, C_HITS, C_TRIP, false, DEBUG>(g, sm, C, P, f);
     if (r == PENDING) r = frame_back<CtaGroup<NT>, SmCta, C_TRIP, C_TRK, C_COMBO, false, DEBUG>(g, sm, C, P, f);
     finish_frame(g, sm, P, f, r);

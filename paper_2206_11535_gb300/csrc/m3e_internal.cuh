@@ -18,7 +18,6 @@ constexpr int DEFERRED = -1;      // process_frame result: frame too large for t
 constexpr int W_HITS = 160, W_TRIP = 160, W_TRK = 48, W_COMBO = 512;
 constexpr int W_P01 = 512, W_P12 = 1024;  // warp stage: Phi-cut partner lists
 constexpr int C_HITS = 4096, C_TRIP = 1024, C_TRK = 128, C_COMBO = 1024;
-constexpr int S1_HITS = W_HITS;   // staged form: sorted-hit slot per frame (stage 1 defers larger frames)
 constexpr int WARPS_PER_CTA = 4;  // persistent warp kernel: warps (frames in flight) per CTA
 constexpr int CTA_THREADS = 256;  // large-frame kernel
 constexpr int PLAIN_THREADS = 128;  // plain per-frame kernel
@@ -55,18 +54,27 @@ struct KParams {
   unsigned long long* stats;  // m3e_stats viewed as an array, or nullptr
   const float4* col_lut;      // per global column: x, y, phi, 0
   const float* row_lut;       // per row: z
-  int* work;                  // [0] work-queue head, [1] deferred count
+  int* work;                  // [0] work-queue head of a frame-parallel kernel
   int* err;                   // error flags (ERR_*), latched until m3e_check
-  int* defer_list;            // frame ids for the CTA stage
+  int* defer_list;            // frames a kernel cannot finish are appended here ...
+  int* defer_count;           // ... and counted here
+  const int* in_list;         // list-driven kernels: the frames to run ...
+  const int* in_count;        // ... and their number
   int grab;                   // frames per work-queue grab
+  int defer_hits;             // warp stages defer frames with more hits (<= W_HITS)
   m3e_dump dump;              // all pointers null unless debugging
 };
 
 // Global scratch of the staged form (see m3e_staged.cu), sized per batch.
 struct SParams {
-  float *hx, *hy, *hz, *hphi;  // sorted hits of each pending frame, slot f * S1_HITS
+  float *hx, *hy, *hz, *hphi;  // sorted hits of the pending frames (from the hit allocator)
   uint32_t* haddr;
   uint16_t* hidx;              // input index of each sorted hit (candidate record only)
+  long long* fhbase;           // per frame: first sorted hit
+  int* list1;                  // frames deferred by the warp tier of stage 1
+  int* list1b;                 // frames deferred by the middle tier of stage 1
+  int* list2;                  // frames deferred by the top tier of stage 1 and by stage 3
+  int* lcount;                 // [0] list1 count, [1] list2 count, [2] list1b count
   uint16_t* l3;                // [F][NB + 1] layer-3 phi-bin starts, frame-relative
   int *fstate, *ftbase, *fntrip, *ffound;  // per frame: state, triplet range, vertex found
   long long* fcbase;           // per frame: first combination
@@ -75,8 +83,8 @@ struct SParams {
   uint8_t* tstatus;            // per triplet: track status
   float4* trec;                // per triplet: 16-float track record when kept
   int4* combo;                 // {frame, triplet a, triplet b, triplet e-}, frame -1 = unused
-  unsigned long long* counters;  // [0] triplets appended, [1] combinations appended, [2] stage-3 queue
-  int64_t trip_cap, combo_cap;
+  unsigned long long* counters;  // [0] triplets, [1] combinations, [2] stage-3 queue, [3] sorted hits
+  int64_t trip_cap, combo_cap, hits_cap;
 };
 
 enum { ST_FRAMES = 0, ST_HITS, ST_PAIRS, ST_TTESTS, ST_TRIP, ST_TRK, ST_ETEST, ST_COMBO, ST_VTX, ST_DEFER,
@@ -88,8 +96,9 @@ enum { ERR_BADHIT = 1, ERR_NEGSIZE = 2 };
 cudaError_t launch_fused(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
 cudaError_t launch_deferred(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
 cudaError_t launch_plain(const DevCfg& c, const KParams& p, bool debug, cudaStream_t s);
-cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[4], bool debug,
+cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
                           cudaStream_t st, cudaEvent_t* ev);
+size_t stage1c_smem_bytes();
 int fused_blocks_per_sm();
 int stage_blocks_per_sm(int stage);
 size_t fused_smem_bytes();

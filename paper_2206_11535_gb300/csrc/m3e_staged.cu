@@ -17,8 +17,11 @@ namespace m3e {
 namespace {
 
 constexpr int NL3 = NB + 1;                        // layer-3 bin starts per frame
-constexpr int S1_TRIP = 256;                       // stage-1 triplet capacity (hits: S1_HITS)
-using SmFront = FrameSm<S1_HITS, S1_TRIP, 1, 1>;
+constexpr int S1_TRIP = 256;                       // stage-1 warp-tier triplet capacity
+using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1>;
+constexpr int M_HITS = 1024;                       // stage-1 middle tier (CTA per frame)
+using SmFrontMid = FrameSm<M_HITS, C_TRIP, 1, 1>;
+using SmFrontCta = FrameSm<C_HITS, C_TRIP, 1, 1>;
 constexpr int S3_WARPS = 4;
 
 struct S3Sm {                                      // stage 3, per warp
@@ -36,12 +39,83 @@ __device__ __forceinline__ int warp_count_add(int* ctr, bool pred) {  // ordered
   return base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
 }
 
-// ---- stage 1
+// ---- stage 1: write-out of a frame whose cuts selected triplets
+// Sorted hits and triplets go to global memory at places taken from the hit and
+// triplet allocators; a frame that does not fit is deferred (returns false).
+template <class G, class Sm, bool DEBUG>
+__device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const KParams& P, const SParams& S, int f, int n,
+                                           int ntrip, long long* bcast) {
+  if (g.leader()) {
+    bcast[0] = (long long)atomicAdd(&S.counters[3], (unsigned long long)n);
+    bcast[1] = (long long)atomicAdd(&S.counters[0], (unsigned long long)ntrip);
+  }
+  g.sync();
+  const long long hb = bcast[0], tb = bcast[1];
+  g.sync();
+  if (hb + n > S.hits_cap || tb + ntrip > S.trip_cap) {
+    // out of space: mark the triplet slots this frame owns below the cap as unused
+    for (int64_t t = tb + g.rank(); t < S.trip_cap && t < tb + ntrip; t += G::N) S.trip[t] = make_int4(-1, 0, 0, 0);
+    return false;
+  }
+  for (int i = g.rank(); i < n; i += G::N) {
+    S.hx[hb + i] = sm.x[i];
+    S.hy[hb + i] = sm.y[i];
+    S.hz[hb + i] = sm.z[i];
+    S.hphi[hb + i] = sm.phi[i];
+    S.haddr[hb + i] = sm.addr[i];
+    if (DEBUG) S.hidx[hb + i] = sm.inidx[i];
+  }
+  for (int b = g.rank(); b < NL3; b += G::N) S.l3[(int64_t)f * NL3 + b] = sm.bstart[3 * NB + b];
+  for (int t = g.rank(); t < ntrip; t += G::N) {
+    const ushort4 q = sm.u.trip[t];
+    S.trip[tb + t] = make_int4(f, q.x, q.y, q.z);
+  }
+  if (g.leader()) {
+    S.fstate[f] = PENDING;
+    S.fhbase[f] = hb;
+    S.ftbase[f] = (int)tb;
+    S.fntrip[f] = ntrip;
+    S.ffound[f] = 0;
+  }
+  return true;
+}
+
+// After frame_front: decide, emit, or defer one frame (stage-1 tiers).
+template <class G, class Sm, bool DEBUG>
+__device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const KParams& P, const SParams& S, int f, int r,
+                                              long long* bcast) {
+  const int ntrip = sm.ntrip;
+  if (r == PENDING && ntrip == 0) r = M3E_DROP;  // no triplet: no track, no vertex
+  if (r == PENDING) {
+    const int n = (int)(P.off[f + 1] - P.off[f]);
+    if (emit_frame<G, Sm, DEBUG>(g, sm, P, S, f, n, ntrip, bcast)) {
+      if (g.leader() && P.stats)
+        for (int k = 0; k < ST_REASON0; ++k) sm.acc[k] += sm.facc[k];
+    } else {
+      r = DEFERRED;
+    }
+  }
+  if (r == DEFERRED) {
+    if (g.leader()) {
+      S.fstate[f] = DEFERRED;
+      const int k = atomicAdd(P.defer_count, 1);
+      P.defer_list[k] = f;
+      if (P.stats) sm.acc[ST_DEFER] += 1;
+    }
+  } else if (r != PENDING) {
+    if (g.leader()) S.fstate[f] = r;
+    finish_frame(g, sm, P, f, r);
+  }
+  g.sync();
+}
+
+// ---- stage 1, warp tier: one warp per frame, frames from the device queue
 template <bool DEBUG>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     k_stage1(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmFront& sm = reinterpret_cast<SmFront*>(smem_raw)[threadIdx.x >> 5];
+  __shared__ long long bcast[WARPS_PER_CTA][2];
   const WarpGroup g;
   clear_stats(g, sm);
   const int nf = (int)P.n_frames;
@@ -52,56 +126,30 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     if (f0 >= nf) break;
     const int f1 = min(f0 + P.grab, nf);
     for (int f = f0; f < f1; ++f) {
-      int r = frame_front<WarpGroup, SmFront, S1_HITS, S1_TRIP, true, DEBUG>(g, sm, C, P, f);
-      const int ntrip = sm.ntrip;
-      if (r == PENDING && ntrip == 0) r = M3E_DROP;  // no triplet: no track, no vertex
-      if (r == PENDING) {
-        long long tb = 0;
-        if (g.leader()) tb = (long long)atomicAdd(&S.counters[0], (unsigned long long)ntrip);
-        tb = __shfl_sync(FULL, tb, 0);
-        if (tb + ntrip > S.trip_cap) {
-          // out of candidate space: mark the slots this frame owns below the cap, defer
-          for (int64_t t = tb + g.rank(); t < S.trip_cap; t += 32) S.trip[t] = make_int4(-1, 0, 0, 0);
-          r = DEFERRED;
-        } else {
-          const int64_t base = (int64_t)f * S1_HITS;
-          const int n = (int)(P.off[f + 1] - P.off[f]);
-          for (int i = g.rank(); i < n; i += 32) {
-            S.hx[base + i] = sm.x[i];
-            S.hy[base + i] = sm.y[i];
-            S.hz[base + i] = sm.z[i];
-            S.hphi[base + i] = sm.phi[i];
-            S.haddr[base + i] = sm.addr[i];
-            if (DEBUG) S.hidx[base + i] = sm.inidx[i];
-          }
-          for (int b = g.rank(); b < NL3; b += 32) S.l3[(int64_t)f * NL3 + b] = sm.bstart[3 * NB + b];
-          for (int t = g.rank(); t < ntrip; t += 32) {
-            const ushort4 q = sm.u.trip[t];
-            S.trip[tb + t] = make_int4(f, q.x, q.y, q.z);
-          }
-          if (g.leader()) {
-            S.fstate[f] = PENDING;
-            S.ftbase[f] = (int)tb;
-            S.fntrip[f] = ntrip;
-            S.ffound[f] = 0;
-            if (P.stats)
-              for (int k = 0; k < ST_REASON0; ++k) sm.acc[k] += sm.facc[k];
-          }
-        }
-      }
-      if (r == DEFERRED) {
-        if (g.leader()) {
-          S.fstate[f] = DEFERRED;
-          const int k = atomicAdd(&P.work[1], 1);
-          P.defer_list[k] = f;
-          if (P.stats) sm.acc[ST_DEFER] += 1;
-        }
-      } else if (r != PENDING) {
-        if (g.leader()) S.fstate[f] = r;
-        finish_frame(g, sm, P, f, r);
-      }
-      g.sync();
+      const int r = frame_front<WarpGroup, SmFront, W_HITS, S1_TRIP, true, DEBUG>(g, sm, C, P, f);
+      stage1_finish<WarpGroup, SmFront, DEBUG>(g, sm, P, S, f, r, bcast[threadIdx.x >> 5]);
     }
+  }
+  flush_stats(g, sm, P.stats);
+}
+
+// ---- stage 1, CTA tiers: one CTA per frame deferred by the tier below (large
+// frames); the middle tier stages up to M_HITS hits, the top tier C_HITS.
+template <class Sm, int CH, bool DEBUG>
+__global__ void __launch_bounds__(CTA_THREADS)
+    k_stage1c(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sm& sm = *reinterpret_cast<Sm*>(smem_raw);
+  __shared__ long long bcast[2];
+  const CtaGroup<CTA_THREADS> g;
+  clear_stats(g, sm);
+  const int count = *P.in_count;
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const int f = P.in_list[i];
+    int r;
+    if (CH < C_HITS && P.off[f + 1] - P.off[f] > CH) r = DEFERRED;  // for the next tier
+    else r = frame_front<CtaGroup<CTA_THREADS>, Sm, CH, C_TRIP, false, DEBUG>(g, sm, C, P, f);
+    stage1_finish<CtaGroup<CTA_THREADS>, Sm, DEBUG>(g, sm, P, S, f, r, bcast);
   }
   flush_stats(g, sm, P.stats);
 }
@@ -115,7 +163,7 @@ __global__ void __launch_bounds__(128)
     const int4 r = S.trip[i];
     const int f = r.x;
     if (f < 0) continue;
-    const int64_t base = (int64_t)f * S1_HITS;
+    const int64_t base = S.fhbase[f];
     const GHits v{S.hx + base, S.hy + base, S.hz + base, S.hphi + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
     float tk[14];
     const TrackOut o = build_track(v, C, r.y, r.z, r.w, tk);
@@ -262,7 +310,7 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
       if (r == DEFERRED) {
         if (lane == 0) {
           S.fstate[f] = DEFERRED;
-          const int k = atomicAdd(&P.work[1], 1);
+          const int k = atomicAdd(P.defer_count, 1);
           P.defer_list[k] = f;
           if (stats) sm.acc[ST_DEFER] += 1;
         }
@@ -407,6 +455,8 @@ cudaError_t set_smem(K k, size_t bytes) {
 }  // namespace
 
 size_t stage1_smem_bytes() { return sizeof(SmFront) * WARPS_PER_CTA; }
+size_t stage1c_smem_bytes() { return sizeof(SmFrontCta); }
+size_t stage1m_smem_bytes() { return sizeof(SmFrontMid); }
 
 int stage_blocks_per_sm(int stage) {
   int nb = 0;
@@ -418,33 +468,69 @@ int stage_blocks_per_sm(int stage) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage2<false>, 128, 0);
   } else if (stage == 3) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage3<false>, S3_WARPS * 32, 0);
-  } else {
+  } else if (stage == 4) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage4<false>, S4_WARPS * 32, 0);
+  } else if (stage == 5) {
+    set_smem(k_stage1c<SmFrontCta, C_HITS, false>, stage1c_smem_bytes());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1c<SmFrontCta, C_HITS, false>, CTA_THREADS,
+                                                      stage1c_smem_bytes());
+  } else {
+    set_smem(k_stage1c<SmFrontMid, M_HITS, false>, stage1m_smem_bytes());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1c<SmFrontMid, M_HITS, false>, CTA_THREADS,
+                                                      stage1m_smem_bytes());
   }
   return e == cudaSuccess && nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[4], bool debug,
+// Stage 1 (warp tier; middle CTA tier over the warp tier's deferred frames; top
+// CTA tier over the middle tier's), stages 2-5.  grids: stage 1 warp tier, 2, 3,
+// 4, stage 1 top tier, stage 1 middle tier.  Frames deferred by the top tier or by
+// stage 3 end up in S.list2 for the caller's CTA-per-frame kernel.  ev (9 events or
+// null): before stage 1 and after each kernel.
+cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
                           cudaStream_t st, cudaEvent_t* ev) {
-  const size_t sm1 = stage1_smem_bytes();
+  const size_t sm1 = stage1_smem_bytes(), smc = stage1c_smem_bytes(), smm = stage1m_smem_bytes();
   cudaError_t e = debug ? set_smem(k_stage1<true>, sm1) : set_smem(k_stage1<false>, sm1);
+  if (e == cudaSuccess)
+    e = debug ? set_smem(k_stage1c<SmFrontCta, C_HITS, true>, smc) : set_smem(k_stage1c<SmFrontCta, C_HITS, false>, smc);
+  if (e == cudaSuccess)
+    e = debug ? set_smem(k_stage1c<SmFrontMid, M_HITS, true>, smm) : set_smem(k_stage1c<SmFrontMid, M_HITS, false>, smm);
   if (e != cudaSuccess) return e;
+  KParams p1 = p, pm = p, pc = p, p3 = p;
+  p1.defer_list = s.list1;
+  p1.defer_count = s.lcount;
+  pm.in_list = s.list1;
+  pm.in_count = s.lcount;
+  pm.defer_list = s.list1b;
+  pm.defer_count = s.lcount + 2;
+  pc.in_list = s.list1b;
+  pc.in_count = s.lcount + 2;
+  pc.defer_list = s.list2;
+  pc.defer_count = s.lcount + 1;
+  p3.defer_list = s.list2;
+  p3.defer_count = s.lcount + 1;
   if (ev) cudaEventRecord(ev[0], st);
-  if (debug) k_stage1<true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p, s);
-  else k_stage1<false><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p, s);
+  if (debug) k_stage1<true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
+  else k_stage1<false><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   if (ev) cudaEventRecord(ev[1], st);
+  if (debug) k_stage1c<SmFrontMid, M_HITS, true><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
+  else k_stage1c<SmFrontMid, M_HITS, false><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
+  if (ev) cudaEventRecord(ev[2], st);
+  if (debug) k_stage1c<SmFrontCta, C_HITS, true><<<grids[4], CTA_THREADS, smc, st>>>(c, pc, s);
+  else k_stage1c<SmFrontCta, C_HITS, false><<<grids[4], CTA_THREADS, smc, st>>>(c, pc, s);
+  if (ev) cudaEventRecord(ev[3], st);
   if (debug) k_stage2<true><<<grids[1], 128, 0, st>>>(c, p, s);
   else k_stage2<false><<<grids[1], 128, 0, st>>>(c, p, s);
-  if (ev) cudaEventRecord(ev[2], st);
-  if (debug) k_stage3<true><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p, s);
-  else k_stage3<false><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p, s);
-  if (ev) cudaEventRecord(ev[3], st);
+  if (ev) cudaEventRecord(ev[4], st);
+  if (debug) k_stage3<true><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p3, s);
+  else k_stage3<false><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p3, s);
+  if (ev) cudaEventRecord(ev[5], st);
   if (debug) k_stage4<true><<<grids[3], S4_WARPS * 32, 0, st>>>(c, p, s);
   else k_stage4<false><<<grids[3], S4_WARPS * 32, 0, st>>>(c, p, s);
-  if (ev) cudaEventRecord(ev[4], st);
+  if (ev) cudaEventRecord(ev[6], st);
   const int g5 = (int)((p.n_frames + 255) / 256);
   if (g5 > 0) k_stage5<<<g5, 256, 0, st>>>(p, s);
-  if (ev) cudaEventRecord(ev[5], st);
+  if (ev) cudaEventRecord(ev[7], st);
   return cudaGetLastError();
 }
 

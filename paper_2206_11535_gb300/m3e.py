@@ -250,9 +250,10 @@ class Context:
         _check(lib.m3e_set_profiling(self._h, int(on)))
 
     def stage_times(self) -> list[float]:
-        """ms of stages 1-5 and of the deferred-frame kernel of the last timed staged call."""
-        a = (C.c_float * 6)()
-        _check(lib.m3e_stage_times(self._h, a, 6))
+        """ms of stage 1 (warp, middle and top tiers), stages 2-5 and the deferred-frame
+        kernel of the last timed staged call."""
+        a = (C.c_float * 8)()
+        _check(lib.m3e_stage_times(self._h, a, 8))
         return list(a)
 
     def kernel_times(self) -> tuple[float, float]:

@@ -220,3 +220,17 @@ def test_stats_counters(ctx, m3e, ocfg, form):
     _, _, cnt = O.select_frames(ocfg, d["hits"], d["off"], 4, counts=True)
     assert abs(s["triplets"] - cnt[:, 3].sum()) <= 5
     assert abs(s["tracks"] - cnt[:, 4].sum()) <= 5
+
+
+def test_c3_uneven_frames_sample(ctx, ocfg):
+    """Frames of the uneven workload (lognormal track counts, some at 100x noise):
+    the staged form with its CTA tier for large frames, checked candidate by
+    candidate, and the plain form deciding identically."""
+    d = gen.workload("c3", n_frames=400, seed=33)
+    assert (np.diff(d["off"]) > 160).sum() > 20  # the CTA tier of stage 1 is exercised
+    hits, off = _dev(d)
+    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024, form=FORMS["staged"]))
+    s = _check_results(P.compare_batch(ocfg, d["hits"], d["off"], rec), max_boundary_frac=0.02)
+    print("c3 sample parity", s)
+    keep_p, reason_p = ctx.select_frames_plain(hits, off)
+    assert (reason_p.cpu().numpy() == rec["reason"]).all()
