@@ -180,6 +180,37 @@ int m3e_check(m3e_ctx* ctx, cudaStream_t stream);
  * resident CTAs per SM (0 = as many as fit). */
 int m3e_set_launch(m3e_ctx* ctx, int frames_per_grab, int ctas_per_sm);
 
+/* Size the context's scratch for batches of up to max_frames frames, so that the
+ * select calls that follow allocate nothing (required before m3e_graph_create). */
+int m3e_prepare(m3e_ctx* ctx, int64_t max_frames);
+
+/* One batch as a CUDA graph (the persistent batched form, captured once and
+ * relaunched): form 0 staged, 1 fused.  The graph holds the given pointers and
+ * frame count; relaunching it reruns the selection on whatever those buffers hold.
+ * Needs m3e_prepare(ctx, >= n_frames) beforehand.  The graph shares the context's
+ * scratch: do not run it concurrently with other calls on the same context. */
+typedef struct m3e_graph m3e_graph;
+int m3e_graph_create(m3e_ctx* ctx, int form, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                     uint8_t* d_keep, uint8_t* d_reason, m3e_graph** out);
+int m3e_graph_launch(m3e_graph* graph, cudaStream_t stream);
+int m3e_graph_destroy(m3e_graph* graph);
+
+/* Launch parameters chosen by m3e_autotune and in force in the context. */
+typedef struct {
+  int32_t frames_per_grab;   /* work-queue granularity of the frame-parallel kernels */
+  int32_t defer_hits;        /* frames with more hits go from the warp tier to the CTA tiers */
+  int32_t s1_ctas_per_sm;    /* resident CTAs per SM of the stage-1 warp tier */
+  int32_t configs_tried;
+  float ms_default, ms_best; /* calibration batch time at the defaults and at the choice */
+} m3e_tuning;
+
+/* Time the staged form on a calibration batch (device buffers as for
+ * m3e_select_frames) over a grid of launch parameters and keep the fastest in
+ * the context.  Synchronises the context's device; decisions do not depend on
+ * the parameters. */
+int m3e_autotune(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames, uint8_t* d_keep,
+                 uint8_t* d_reason, m3e_tuning* out);
+
 /* Number of kernel launches the last select call enqueued. */
 int m3e_last_launch_count(const m3e_ctx* ctx);
 

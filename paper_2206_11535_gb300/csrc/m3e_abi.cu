@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -734,5 +735,163 @@ extern "C" int m3e_select_frames_noalloc(m3e_ctx* x, const int32_t* d_hits, cons
   CUDA_TRY(launch_fused(x->dc, p, x->sms * x->fused_bpsm, false, s));
   CUDA_TRY(launch_deferred(x->dc, p, 2 * x->sms, false, s));
   x->last_launches = 2;
+  return M3E_OK;
+}
+
+// ------------------------------------------------------------------ persistent batched form
+
+struct m3e_graph {
+  m3e_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" int m3e_prepare(m3e_ctx* x, int64_t max_frames) {
+  if (!x) return fail(M3E_EINVAL, "ctx is NULL");
+  if (max_frames < 0 || max_frames > (int64_t)1 << 30) return fail(M3E_EINVAL, "max_frames out of range");
+  DeviceGuard guard(x->device);
+  return ensure_scratch(x->main, max_frames > 1 ? max_frames : 1, true);
+}
+
+extern "C" int m3e_graph_create(m3e_ctx* x, int form, const int32_t* d_hits, const int64_t* d_off, int64_t n,
+                                uint8_t* d_keep, uint8_t* d_reason, m3e_graph** out) {
+  if (!x || !out) return fail(M3E_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (form != FORM_STAGED && form != FORM_FUSED) return fail(M3E_EINVAL, "graph form must be 0 (staged) or 1 (fused)");
+  int rc = check_batch(d_hits, d_off, n, d_keep, d_reason);
+  if (rc) return rc;
+  if (n < 1) return fail(M3E_EINVAL, "a graph needs at least one frame");
+  if (n > x->main.defer_cap || (form == FORM_STAGED && n > x->main.frames_cap))
+    return fail(M3E_ESTATE, "call m3e_prepare(ctx, %lld) before capturing", (long long)n);
+  DeviceGuard guard(x->device);
+  m3e_graph* gr = new (std::nothrow) m3e_graph();
+  if (!gr) return fail(M3E_ENOMEM, "graph");
+  gr->ctx = x;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    delete gr;
+    return fail(M3E_ECUDA, "capture stream");
+  }
+  KParams p = base_params(x, x->main);
+  p.hits = d_hits;
+  p.off = d_off;
+  p.n_frames = n;
+  p.keep = d_keep;
+  p.reason = d_reason;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = enqueue(x, x->main, p, form, false, cs, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    gr->graph = g;
+    if (rc == M3E_OK && e2 != cudaSuccess) rc = fail(M3E_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+    if (rc == M3E_OK) {
+      e = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
+      if (e != cudaSuccess) rc = fail(M3E_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+  } else {
+    rc = fail(M3E_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  }
+  cudaStreamDestroy(cs);
+  if (rc) {
+    m3e_graph_destroy(gr);
+    return rc;
+  }
+  *out = gr;
+  return M3E_OK;
+}
+
+extern "C" int m3e_graph_launch(m3e_graph* gr, cudaStream_t s) {
+  if (!gr || !gr->exec) return fail(M3E_EINVAL, "graph is NULL");
+  DeviceGuard guard(gr->ctx->device);
+  CUDA_TRY(cudaGraphLaunch(gr->exec, s));
+  return M3E_OK;
+}
+
+extern "C" int m3e_graph_destroy(m3e_graph* gr) {
+  if (!gr) return M3E_OK;
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  if (gr->graph) cudaGraphDestroy(gr->graph);
+  delete gr;
+  return M3E_OK;
+}
+
+// Autotuner: time the staged form on the calibration batch for each point of a
+// small grid of launch parameters (median of three runs after one warm-up on a
+// private stream) and keep the fastest.
+extern "C" int m3e_autotune(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n, uint8_t* d_keep,
+                            uint8_t* d_reason, m3e_tuning* out) {
+  if (!x || !out) return fail(M3E_EINVAL, "NULL argument");
+  int rc = check_batch(d_hits, d_off, n, d_keep, d_reason);
+  if (rc) return rc;
+  if (n < 1) return fail(M3E_EINVAL, "calibration batch is empty");
+  DeviceGuard guard(x->device);
+  rc = ensure_scratch(x->main, n, true);
+  if (rc) return rc;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const int s1max = stage_blocks_per_sm(1);
+  const int grabs[] = {1, 2, 4, 8, 16};
+  const int dhits[] = {96, 128, W_HITS};
+  const int s1s[] = {s1max, s1max > 2 ? (s1max + 1) / 2 : s1max};
+  const int g0 = x->grab, d0 = x->defer_hits, b0 = x->s1_bpsm;
+  auto run = [&](float* ms) -> int {
+    KParams p = base_params(x, x->main);
+    p.hits = d_hits;
+    p.off = d_off;
+    p.n_frames = n;
+    p.keep = d_keep;
+    p.reason = d_reason;
+    float t[3];
+    int r = enqueue(x, x->main, p, FORM_STAGED, false, st, false);  // warm-up
+    for (int k = 0; k < 3 && r == M3E_OK; ++k) {
+      CUDA_TRY(cudaEventRecord(e0, st));
+      r = enqueue(x, x->main, p, FORM_STAGED, false, st, false);
+      CUDA_TRY(cudaEventRecord(e1, st));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      CUDA_TRY(cudaEventElapsedTime(&t[k], e0, e1));
+    }
+    if (r) return r;
+    std::sort(t, t + 3);
+    *ms = t[1];
+    return M3E_OK;
+  };
+  float ms_def = 0.f;
+  rc = run(&ms_def);
+  float best = ms_def;
+  int bg = g0, bd = d0, bb = b0, tried = 1;
+  for (int g : grabs)
+    for (int d : dhits)
+      for (int b : s1s) {
+        if (rc) break;
+        x->grab = g;
+        x->defer_hits = d;
+        x->s1_bpsm = b;
+        float ms = 0.f;
+        rc = run(&ms);
+        ++tried;
+        if (rc == M3E_OK && ms < best) {
+          best = ms;
+          bg = g;
+          bd = d;
+          bb = b;
+        }
+      }
+  x->grab = bg;
+  x->defer_hits = bd;
+  x->s1_bpsm = bb;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (rc) return rc;
+  out->frames_per_grab = bg;
+  out->defer_hits = bd;
+  out->s1_ctas_per_sm = bb;
+  out->configs_tried = tried;
+  out->ms_default = ms_def;
+  out->ms_best = best;
   return M3E_OK;
 }

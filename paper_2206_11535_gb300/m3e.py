@@ -55,6 +55,11 @@ class Dump(C.Structure):
                 ("n_combo", C.c_void_p), ("combo", C.c_void_p), ("combo_val", C.c_void_p)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("frames_per_grab", C.c_int32), ("defer_hits", C.c_int32), ("s1_ctas_per_sm", C.c_int32),
+                ("configs_tried", C.c_int32), ("ms_default", C.c_float), ("ms_best", C.c_float)]
+
+
 def _load(path: str = LIB_PATH):
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with paper_2206_11535_gb300.build.build() "
@@ -67,6 +72,11 @@ def _load(path: str = LIB_PATH):
         getattr(lib, name).argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     lib.m3e_select_frames_debug.argtypes = [vp, C.c_int, vp, vp, i64, vp, vp, C.POINTER(Dump), vp]
     lib.m3e_stage_times.argtypes = [vp, C.POINTER(C.c_float), C.c_int]
+    lib.m3e_prepare.argtypes = [vp, i64]
+    lib.m3e_graph_create.argtypes = [vp, C.c_int, vp, vp, i64, vp, vp, C.POINTER(vp)]
+    lib.m3e_graph_launch.argtypes = [vp, vp]
+    lib.m3e_graph_destroy.argtypes = [vp]
+    lib.m3e_autotune.argtypes = [vp, vp, vp, i64, vp, vp, C.POINTER(Tuning)]
     lib.m3e_select_frames_host.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.m3e_select_frames_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.m3e_check.argtypes = [vp, vp]
@@ -240,6 +250,21 @@ class Context:
         _check(lib.m3e_check(self._h, _stream(stream)))
         return OK
 
+    def prepare(self, max_frames: int):
+        """``m3e_prepare``: size the scratch for batches of up to max_frames frames."""
+        _check(lib.m3e_prepare(self._h, max_frames))
+
+    def graph(self, hits, off, keep, reason, form=STAGED) -> "Graph":
+        """``m3e_graph_create``: one batch captured as a CUDA graph."""
+        return Graph(self, hits, off, keep, reason, form)
+
+    def autotune(self, hits, off, keep=None, reason=None) -> dict:
+        """``m3e_autotune`` on a calibration batch; returns the chosen parameters."""
+        nf, keep, reason = self._outs(hits, off, keep, reason)
+        t = Tuning()
+        _check(lib.m3e_autotune(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
     def set_launch(self, frames_per_grab: int, ctas_per_sm: int = 0):
         _check(lib.m3e_set_launch(self._h, frames_per_grab, ctas_per_sm))
 
@@ -261,6 +286,32 @@ class Context:
         a, b = C.c_float(), C.c_float()
         _check(lib.m3e_kernel_times(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+
+class Graph:
+    """A batch captured as a CUDA graph (``m3e_graph_*``); keeps its buffers alive."""
+
+    def __init__(self, ctx: Context, hits, off, keep, reason, form=STAGED):
+        self._bufs = (hits, off, keep, reason)
+        self.ctx = ctx
+        h = C.c_void_p()
+        _check(lib.m3e_graph_create(ctx._h, form, _ptr(hits), _ptr(off), off.numel() - 1, _ptr(keep), _ptr(reason),
+                                    C.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib.m3e_graph_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.m3e_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stats_dict(t) -> dict:

@@ -234,3 +234,28 @@ def test_c3_uneven_frames_sample(ctx, ocfg):
     print("c3 sample parity", s)
     keep_p, reason_p = ctx.select_frames_plain(hits, off)
     assert (reason_p.cpu().numpy() == rec["reason"]).all()
+
+
+def test_graph_and_autotune_keep_decisions(m3e, cfg):
+    """The persistent batched form: autotuned launch parameters and a captured CUDA
+    graph (staged and fused) give the decisions of a direct call."""
+    d = gen.workload("c3", n_frames=3000, seed=34)
+    hits, off = _dev(d)
+    nf = d["off"].size - 1
+    with m3e.Context(cfg, 0) as ctx:
+        ref = ctx.select_frames(hits, off)[1].cpu().numpy()
+        t = ctx.autotune(hits, off)
+        assert t["configs_tried"] > 10 and t["ms_best"] <= t["ms_default"] * 1.05
+        assert (ctx.select_frames(hits, off)[1].cpu().numpy() == ref).all()
+        ctx.prepare(nf)
+        for form in (m3e.STAGED, m3e.FUSED):
+            keep = torch.empty(nf, dtype=torch.uint8, device="cuda")
+            reason = torch.empty(nf, dtype=torch.uint8, device="cuda")
+            g = ctx.graph(hits, off, keep, reason, form=form)
+            for _ in range(2):
+                reason.fill_(9)
+                g.launch()
+                torch.cuda.synchronize()
+                assert (reason.cpu().numpy() == ref).all()
+            g.close()
+        ctx.check()
