@@ -54,12 +54,28 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters (no autotuner)")
+    ap.add_argument("--arms", default="main,forms,e2e,c3,c5",
+                    help="comma list of measurements: main (staged, always), forms (fused and plain), e2e, c3, "
+                         "c5 (streaming latency)")
+    ap.add_argument("--c5-frames", type=int, default=1_000_000)
     return ap.parse_args()
 
 
 def shard_seed(rank: int) -> int:
     """Weak scaling: rank r selects its own batch (seed 2 on rank 0)."""
     return 2 + 7919 * rank
+
+
+def max_over_ranks(ms: float, device, world: int) -> float:
+    """The job's time is the slowest rank's: max-reduce one float over the process group."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def make_batch(n_frames: int, rank: int):
@@ -120,9 +136,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(n_frames: int):
-    """DRAM bytes of one staged batch (all stage kernels) from the committed ncu summary,
-    scaled to n_frames; None when the summary was taken on other kernel sources."""
+def recorded_traffic(n_frames: int, stage: str):
+    """DRAM bytes (read + write) of one batch's launches of the given stage, from the committed
+    ncu summary (bytes per frame of a smaller batch of the same workload, scaled to n_frames);
+    None when the summary was taken on other kernel sources."""
     p = os.path.join(ROOT, "profiles", "staged_c2_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -134,7 +151,7 @@ def recorded_traffic(n_frames: int):
     if kv.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_frame"]) * n_frames
+        return float(kv["dram_bytes_per_frame." + stage]) * n_frames
     except (KeyError, ValueError):
         return None
 
@@ -190,6 +207,39 @@ def run_reference(args, rank, world):
           flush=True)
 
 
+C5_RATES = (15.625e6 / 12, 15.625e6 / 4, 15.625e6)
+
+
+def stream_arm(ctx, gen, n_frames: int, dev) -> dict:
+    """Latency of the streaming path on the c5 frame mix at three arrival rates."""
+    import torch
+    d = gen.workload("c5", n_frames=n_frames)
+    keep, reason = ctx.select_frames_fused(torch.from_numpy(d["hits"]).to(dev), torch.from_numpy(d["off"]).to(dev))
+    ref = reason.cpu().numpy()
+    ctx.stream_open()
+    ctx.stream_replay(d["hits"], d["off"][:20001], rate_hz=1e6, seed=99)  # warm-up
+    rates = []
+    for k, rate in enumerate(C5_RATES):
+        r = ctx.stream_replay(d["hits"], d["off"], rate_hz=rate, seed=5 + k)
+        q = lambda a, p: float(np.percentile(a, p)) / 1e3  # noqa: E731  (microseconds)
+        rates.append({"offered_frames_per_s": rate, "sustained_frames_per_s": r["sustained_hz"],
+                      "submitted_frames_per_s": r["submit_hz"], "busy_retries": int(r["busy_retries"]),
+                      "kernel_launches": int(r["kernel_launches"]),
+                      "latency_submit_us": {"p50": q(r["lat_submit_ns"], 50), "p99": q(r["lat_submit_ns"], 99),
+                                            "p99.9": q(r["lat_submit_ns"], 99.9)},
+                      "latency_arrival_us": {"p50": q(r["lat_arrival_ns"], 50), "p99": q(r["lat_arrival_ns"], 99),
+                                             "p99.9": q(r["lat_arrival_ns"], 99.9)},
+                      "kept_fraction": float(r["keep"].mean()),
+                      "identical_to_batch": bool((r["reason"] == ref).all())})
+    st = ctx.stream_poll()
+    ctx.stream_close()
+    return {"workload": f"c5: {n_frames:,} frames of the c1 mix (Poisson(10) tracks, 0.5 noise/layer, "
+                        "signal every 10th frame), seed 5; Poisson arrivals, one submitting host thread",
+            "latency": "submit: m3e_stream_submit to result delivered into the caller's slot; arrival: "
+                       "scheduled arrival to result (includes waiting for admission)",
+            "rates": rates, "heavy_frames": int(st["heavy_frames"])}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -224,9 +274,10 @@ def main():
     ctx = m3e.Context(cfg, local)
     stream = torch.cuda.current_stream(dev)
 
-    # launch parameters from the library's autotuner on a calibration slice (the first 50,000 frames)
-    ncal = min(nf, 50000)
-    tuning = ctx.autotune(hits, off[:ncal + 1])
+    # launch parameters from the library's autotuner on a calibration slice (the first 250,000 frames)
+    arms = set(args.arms.split(","))
+    ncal = min(nf, 250000)
+    tuning = None if args.no_tune else ctx.autotune(hits, off[:ncal + 1])
     # work counts of this batch (untimed) for the algorithmic operation count
     st = m3e.new_stats(dev)
     ctx.select_frames(hits, off, keep, reason, stats=st)
@@ -248,12 +299,7 @@ def main():
                 ks.append(ctx.stage_times())
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, ks
+        return max_over_ranks(e0.elapsed_time(e1), dev, world), ks
 
     # main arm: the staged form, back to back, SM clocks sampled during the timed region
     with Clocks(local) as clk:
@@ -266,11 +312,18 @@ def main():
     ctx.set_profiling(False)
     # the fused (one persistent kernel, warp per frame) and plain (CTA per frame) forms
     alt_steps = max(2, args.steps // 2)
-    ms_fused, _ = timed(lambda: ctx.select_frames_fused(hits, off, keep, reason, stream=stream), alt_steps, 1)
-    ms_plain, _ = timed(lambda: ctx.select_frames_plain(hits, off, keep, reason, stream=stream), alt_steps, 1)
+    forms = None
+    if "forms" in arms:
+        ms_fused, _ = timed(lambda: ctx.select_frames_fused(hits, off, keep, reason, stream=stream), alt_steps, 1)
+        ms_plain, _ = timed(lambda: ctx.select_frames_plain(hits, off, keep, reason, stream=stream), alt_steps, 1)
+        forms = {"fused_form": {"value": world * nf * alt_steps / (ms_fused / 1e3), "unit": "frames/s",
+                                "ms_per_step": ms_fused / alt_steps},
+                 "plain_per_frame": {"value": world * nf * alt_steps / (ms_plain / 1e3), "unit": "frames/s",
+                                     "ms_per_step": ms_plain / alt_steps,
+                                     "speedup_of_staged": (ms_plain / alt_steps) / (ms / args.steps)}}
     # end to end from pinned host memory through the C ABI host entry point
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and "e2e" in arms:
         hh = torch.from_numpy(d["hits"]).pin_memory()
         ho = torch.from_numpy(d["off"]).pin_memory()
         hk = torch.empty(nf, dtype=torch.uint8).pin_memory()
@@ -281,7 +334,7 @@ def main():
                "ms_per_step": ms_e2e / args.steps}
     # uneven frames (lognormal track counts, 1 % of frames at 100x noise): staged vs plain
     c3 = None
-    if not args.no_c3:
+    if not args.no_c3 and "c3" in arms:
         dc = gen.workload("c3", seed=3 + 7919 * rank)
         h3 = torch.from_numpy(dc["hits"]).to(dev)
         o3 = torch.from_numpy(dc["off"]).to(dev)
@@ -289,7 +342,7 @@ def main():
         k3 = torch.empty(n3, dtype=torch.uint8, device=dev)
         r3 = torch.empty(n3, dtype=torch.uint8, device=dev)
         # the persistent batched form: autotuned on a calibration slice, the batch captured as one graph
-        tune3 = ctx.autotune(h3, o3[:20001])
+        tune3 = None if args.no_tune else ctx.autotune(h3, o3[:min(n3, 50000) + 1])
         ctx.set_profiling(True)
         _, k3s = timed(lambda: ctx.select_frames(h3, o3, k3, r3, stream=stream), 3, 1, profile=True)
         ctx.set_profiling(False)
@@ -310,7 +363,8 @@ def main():
               "frames_over_160_hits": int((np.diff(dc["off"]) > 160).sum())}
         graph3.close()
         del h3, o3
-        ctx.autotune(hits, off[:ncal + 1])  # back to the main batch's parameters
+        if tuning is not None:
+            ctx.autotune(hits, off[:ncal + 1])  # back to the main batch's parameters
     # the main arm's decisions are those of the last timed staged call
     ctx.select_frames(hits, off, keep, reason, stream=stream)
     ctx.check()
@@ -330,13 +384,18 @@ def main():
     stages.append({"kernel": "deferred frames (CTA per frame)", "ms": float(st_ms[7])})
     stages[0]["ms_tiers"] = [float(st_ms[0]), float(st_ms[1]), float(st_ms[2])]
     dom = max(stages[:5], key=lambda x: x["ms"])
-    tr = recorded_traffic(nf)
+    tr = recorded_traffic(nf, dom["kernel"].split()[0])
     roof = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
             "frac": dom["frac_of_peak"], "traffic": tr, "kernel_ms": dom["ms"],
             "peak_source": f"FP32 lanes x 2 x SM clock: {props.multi_processor_count} SMs x 128 x 2 x "
                            f"{f_mhz:.0f} MHz (median sampled under load)",
             "stages": stages,
             "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf}
+    # streaming (c5): open-loop Poisson arrivals at the frame rates of 1e8 muons/s
+    # (64 ns frames) divided by 12, 4 and 1, frame by frame through m3e_stream_submit
+    c5 = None
+    if "c5" in arms and world == 1:
+        c5 = stream_arm(ctx, gen, args.c5_frames, dev)
     out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -345,15 +404,12 @@ def main():
                       "form": "staged: 5 persistent kernels regrouping the batch by candidate",
                       "parallelism": f"{world} independent GPU shard(s), no collective on the data path"},
            "hits_per_s": world * nh * args.steps / (ms / 1e3),
-           "fused_form": {"value": world * nf * alt_steps / (ms_fused / 1e3), "unit": "frames/s",
-                          "ms_per_step": ms_fused / alt_steps},
-           "plain_per_frame": {"value": world * nf * alt_steps / (ms_plain / 1e3), "unit": "frames/s",
-                               "ms_per_step": ms_plain / alt_steps,
-                               "speedup_of_staged": (ms_plain / alt_steps) / (ms / args.steps)},
+           **(forms or {}),
            "kept_fraction": float(keep.float().mean().item()),
            "reasons": dict(zip(m3e.REASONS, stats["reasons"][:7])),
            "tuning": tuning,
            "uneven_frames_c3": c3,
+           "streaming_c5": c5,
            "roofline": roof, "e2e": e2e, "clocks": cl, "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(d)

@@ -207,7 +207,10 @@ typedef struct {
 /* Time the staged form on a calibration batch (device buffers as for
  * m3e_select_frames) over a grid of launch parameters and keep the fastest in
  * the context.  Synchronises the context's device; decisions do not depend on
- * the parameters. */
+ * the parameters.  Each configuration is timed as the median of five runs
+ * after a warm-up; one replaces the current choice only when it is more than
+ * 2% faster, so a calibration batch of a few ms keeps the defaults unless a
+ * change clearly pays. */
 int m3e_autotune(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames, uint8_t* d_keep,
                  uint8_t* d_reason, m3e_tuning* out);
 
@@ -245,6 +248,114 @@ int m3e_stage_times(m3e_ctx* ctx, float* ms, int n);
  *   - No statistics or candidate record. */
 int m3e_select_frames_noalloc(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
                               uint8_t* d_keep, uint8_t* d_reason, cudaStream_t stream);
+
+/* ------------------------------------------------------------------ streaming
+ *
+ * Frame-by-frame submission with continuous batching: the filter-farm setting
+ * of the paper (Sec. "Implementation": frames arrive continuously from the
+ * readout and are selected as they come).  Every 64 ns frame is handed over as
+ * its own packet; a resident kernel selects frames while new ones are admitted,
+ * so there is no batch boundary to wait for.
+ *
+ * How it works:
+ *   - m3e_stream_submit copies the packet into a ring of pinned host memory and
+ *     publishes a descriptor with a store-release.  It never calls CUDA.
+ *   - A resident kernel (one warp per frame, the fused per-frame code) takes
+ *     frames in submission order.  One warp of it moves new descriptors into a
+ *     device ring; each worker warp waits, with bounded back-off, for the frame
+ *     of the ticket it drew, reads the hits over the host link and writes a
+ *     completion word into a pinned completion ring.
+ *   - A library thread delivers completions into the caller's result slots,
+ *     frees ring space in submission order and relaunches the resident kernel
+ *     when it has exited while frames are waiting.
+ *   - Frames with more than 160 hits (beyond the warp stage) are gathered by the
+ *     same thread and run by a CTA-per-frame kernel (same decisions).
+ *
+ * Every device wait is bounded: the resident kernel exits after idle_us
+ * without work and after lifetime_ms in any case, and a worker that waits
+ * longer than wait_limit_ms for a published frame gives up, latches an error
+ * and exits.  Decisions are those of m3e_select_frames_fused for the same
+ * frame, alone or among others. */
+
+/* Result slot of one submitted frame: caller-owned host memory, written by the
+ * library.  done turns from 0 to 1 (store-release) when the other fields are
+ * valid; t_submit_ns is set by m3e_stream_submit, t_done_ns when the library
+ * thread delivers the result (CLOCK_MONOTONIC nanoseconds). */
+typedef struct {
+  volatile uint32_t done;
+  uint8_t keep, reason;      /* as in m3e_select_frames */
+  uint16_t reserved;
+  int32_t err;               /* M3E_OK, M3E_EBADHIT (invalid address), M3E_ETIMEOUT (stream failed) */
+  uint64_t tag;              /* the caller's tag */
+  uint64_t t_submit_ns, t_done_ns;
+} m3e_result;
+
+/* Stream parameters; zero fields take the defaults. */
+typedef struct {
+  uint32_t size;             /* sizeof(m3e_stream_params) */
+  int32_t slots;             /* frames in flight, a power of two (default 65536) */
+  int64_t ring_bytes;        /* host ring of packet bytes (default 64 MiB) */
+  int32_t ctas_per_sm;       /* resident kernel: CTAs of 4 warps per SM (default 2) */
+  int32_t idle_us;           /* resident kernel exits after this long without work (default 20000) */
+  int32_t lifetime_ms;       /* ... and after this long in any case; relaunched while work remains (default 2000) */
+  int32_t wait_limit_ms;     /* a worker's wait for a published frame (default lifetime_ms + 1000) */
+  int32_t no_feeder;         /* test only: 1 = nothing publishes frames to the workers, so their waits expire */
+} m3e_stream_params;
+
+typedef struct {
+  uint64_t submitted, completed, busy_refusals;
+  uint64_t kernel_launches;  /* resident kernel launches so far */
+  uint64_t heavy_frames;     /* frames run by the CTA-per-frame kernel */
+  int32_t kernel_running;    /* resident kernel currently on the GPU */
+  int32_t failed;            /* a device wait expired: frames in flight were lost (M3E_ETIMEOUT) */
+} m3e_stream_status;
+
+/* Start the streaming machinery (pinned rings, device rings, library thread).
+ * params may be NULL for the defaults.  M3E_ESTATE if already open. */
+int m3e_stream_open(m3e_ctx* ctx, const m3e_stream_params* params);
+
+/* Submit one frame: h_packet[0 .. n_hits) packed addresses (any host memory;
+ * copied before return, so the buffer may be reused at once).  h_result_slot
+ * must stay valid until its done flag is 1.  Opens the stream with the defaults
+ * if it is not open.  Returns M3E_EBUSY without side effects when the slots or
+ * the ring bytes are all in use (retry later), M3E_EINVAL for a packet larger
+ * than the ring or a NULL slot, M3E_ETIMEOUT once the stream has failed.
+ * Safe to call from several threads (internally locked). */
+int m3e_stream_submit(m3e_ctx* ctx, const int32_t* h_packet, int32_t n_hits, uint64_t tag,
+                      m3e_result* h_result_slot);
+
+/* Counters of the stream (no wait). */
+int m3e_stream_poll(m3e_ctx* ctx, m3e_stream_status* out);
+
+/* Wait until every submitted frame has its result, at most timeout_ms;
+ * M3E_ETIMEOUT if the time ran out or the stream failed. */
+int m3e_stream_drain(m3e_ctx* ctx, int64_t timeout_ms);
+
+/* Drain (bounded), stop the resident kernel and free the stream.  Results of
+ * frames still in flight after the bounded drain are written with err =
+ * M3E_ETIMEOUT.  Also done by m3e_destroy. */
+int m3e_stream_close(m3e_ctx* ctx);
+
+typedef struct {
+  double offered_hz;         /* arrival rate asked for */
+  double sustained_hz;       /* frames / (last result time - first arrival time) */
+  double submit_hz;          /* frames / (last submit time - first arrival time) */
+  uint64_t busy_retries;     /* submissions refused with M3E_EBUSY and retried */
+  uint64_t kernel_launches;
+  int64_t duration_ns;
+} m3e_replay_stats;
+
+/* Latency harness: replay a CSR batch of host frames as an open-loop Poisson
+ * arrival process of rate_hz (exponential gaps from a seeded counter-based
+ * generator, splitmix64).  One submitting thread waits for each frame's arrival
+ * time and submits it, retrying while the stream is busy.  Per frame it returns
+ * keep and reason, the latency from submission to result (out_lat_submit_ns)
+ * and from the scheduled arrival to result (out_lat_arrival_ns, which includes
+ * any wait for admission).  Any output pointer may be NULL.  Waits at most
+ * 30 s beyond the last arrival for the results (M3E_ETIMEOUT). */
+int m3e_stream_replay(m3e_ctx* ctx, const int32_t* h_hits, const int64_t* h_frame_off, int64_t n_frames,
+                      double rate_hz, uint64_t seed, uint8_t* out_keep, uint8_t* out_reason,
+                      int64_t* out_lat_submit_ns, int64_t* out_lat_arrival_ns, m3e_replay_stats* out);
 
 const char* m3e_last_error_string(void);
 int m3e_version(void);

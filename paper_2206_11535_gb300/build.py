@@ -15,11 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libm3e.so")
-UNITS = ["m3e_staged.cu", "m3e_fused.cu", "m3e_abi.cu"]
+UNITS = ["m3e_staged.cu", "m3e_fused.cu", "m3e_stream.cu", "m3e_abi.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "--prec-div=true", "--prec-sqrt=true", "-ftz=false", "--fmad=true",
-         "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I" + os.path.join(ROOT, "include")]
 
 
 def _stale(target: str, deps: list[str]) -> bool:
@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, src_dir: str = SRC, out: s
                 sys.stderr.write(r.stderr)
     if force or jobs or _stale(out, objs):
         subprocess.check_call([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-cudart", "static",
-                               "-o", out] + objs)
+                               "-Xcompiler", "-pthread", "-o", out] + objs)
     return out
 
 

@@ -646,7 +646,10 @@ constexpr int PENDING = -2;  // frame_front result: triplets selected, later sta
 // Stages A-C of one frame (load, sort, selection cuts).  Returns a final reason,
 // DEFERRED (frame too large for this stage), or PENDING with the selected
 // triplets in sm.u.trip and their count in sm.ntrip.
-template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG>
+// LIVE: the hits sit in a ring that the host rewrites while the kernel runs
+// (streaming), so they are read with loads that bypass the caches instead of
+// the read-only path.
+template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG, bool LIVE = false>
 __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P, int f) {
   const bool stats = P.stats != nullptr;
   const int64_t base = P.off[f] - P.off_base;
@@ -677,7 +680,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
   }
   g.sync();
   for (int i = g.rank(); i < n; i += G::N) {
-    const Dec d = decode(C, (uint32_t)__ldg(hp + i));
+    const Dec d = decode(C, (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i)));
     if (!d.ok) sm.bad = 1;
     else if (n <= CH) atomicAdd(&sm.bcur[d.L * NB + d.b], 1);
   }
@@ -695,7 +698,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
   // ---- B: counting sort by (layer, phi bin)
   bucket_scan(g, sm.bcur, sm.bstart);
   for (int i = g.rank(); i < n; i += G::N) {
-    const uint32_t a = (uint32_t)__ldg(hp + i);
+    const uint32_t a = (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i));
     const Dec d = decode(C, a);
     const int key = d.L * NB + d.b;
     const int pos = atomicAdd(&sm.bcur[key], 1);
@@ -792,8 +795,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
       sm.bad = __any_sync(FULL, over) ? 2 : 0;
       __syncwarp();
       if (sm.bad == 2) {
-        ntt = 0;
-        if (lane != 0) npair = 0;
+        npair = ntt = 0;  // the frame is counted by the stage that takes it over
       } else {
         // C: the flat list of candidate triplets
         int nt = 0;
@@ -834,7 +836,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           if (nt > C.max_trip) break;  // the frame overflows: its decision is known
         }
         if (lane == 0) sm.ntrip = nt;
-        if (lane != 0) npair = ntt = 0;  // counted once per warp
+        // npair and ntt are each lane's share (its layer-1 hits): all lanes add them
       }
     } else {
       // (a frame whose triplet count passed max_trip overflows whatever follows: stop)

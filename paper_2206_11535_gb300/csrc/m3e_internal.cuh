@@ -104,4 +104,19 @@ int stage_blocks_per_sm(int stage);
 size_t fused_smem_bytes();
 size_t cta_smem_bytes();
 
+// Records the calling thread's error message (m3e_last_error_string) and returns code.
+int m3e_set_error(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+
+// Streaming engine (m3e_stream.cu).
+struct StreamEngine;
+int stream_create(int device, int sms, const DevCfg& dc, const KParams& base, const m3e_stream_params* sp,
+                  StreamEngine** out);
+int stream_submit(StreamEngine* e, const int32_t* pkt, int32_t n_hits, uint64_t tag, m3e_result* res);
+int stream_poll(StreamEngine* e, m3e_stream_status* out);
+int stream_drain(StreamEngine* e, int64_t timeout_ms);
+int stream_destroy(StreamEngine* e);
+int stream_replay(StreamEngine* e, const int32_t* hits, const int64_t* off, int64_t n_frames, double rate_hz,
+                  uint64_t seed, uint8_t* out_keep, uint8_t* out_reason, int64_t* lat_submit, int64_t* lat_arrival,
+                  m3e_replay_stats* st);
+
 }  // namespace m3e

@@ -327,7 +327,11 @@ def workload(name: str, n_frames: int | None = None, seed: int | None = None) ->
     """The synthetic workloads: ``c1`` (parity: Poisson(10) tracks, 0.5 noise/layer,
     signal every 10th frame), ``c2`` (throughput: Poisson(20), 2 noise/layer, signal in
     0.1% of frames), ``c3`` (uneven: lognormal(median 15, sigma 1) tracks capped at 400,
-    0.5 noise/layer, 1% of frames at 100x noise)."""
+    0.5 noise/layer, 1% of frames at 100x noise), ``c5`` (streaming: the c1 frame mix,
+    signal every 10th frame, 1,000,000 frames, seed 5; the arrival process is the
+    replay's)."""
+    if name == "c5":
+        return generate(n_frames or 1_000_000, 10.0, 0.5, 10, seed if seed is not None else 5)
     if name == "c1":
         return generate(n_frames or 1000, 10.0, 0.5, 10, seed if seed is not None else 1)
     if name == "c2":

@@ -60,6 +60,29 @@ class Tuning(C.Structure):
                 ("configs_tried", C.c_int32), ("ms_default", C.c_float), ("ms_best", C.c_float)]
 
 
+class Result(C.Structure):
+    """``m3e_result``: one submitted frame's result slot (written by the library)."""
+    _fields_ = [("done", C.c_uint32), ("keep", C.c_uint8), ("reason", C.c_uint8), ("reserved", C.c_uint16),
+                ("err", C.c_int32), ("tag", C.c_uint64), ("t_submit_ns", C.c_uint64), ("t_done_ns", C.c_uint64)]
+
+
+class StreamParams(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("slots", C.c_int32), ("ring_bytes", C.c_int64), ("ctas_per_sm", C.c_int32),
+                ("idle_us", C.c_int32), ("lifetime_ms", C.c_int32), ("wait_limit_ms", C.c_int32),
+                ("no_feeder", C.c_int32)]
+
+
+class StreamStatus(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("busy_refusals", C.c_uint64),
+                ("kernel_launches", C.c_uint64), ("heavy_frames", C.c_uint64), ("kernel_running", C.c_int32),
+                ("failed", C.c_int32)]
+
+
+class ReplayStats(C.Structure):
+    _fields_ = [("offered_hz", C.c_double), ("sustained_hz", C.c_double), ("submit_hz", C.c_double),
+                ("busy_retries", C.c_uint64), ("kernel_launches", C.c_uint64), ("duration_ns", C.c_int64)]
+
+
 def _load(path: str = LIB_PATH):
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with paper_2206_11535_gb300.build.build() "
@@ -84,6 +107,13 @@ def _load(path: str = LIB_PATH):
     lib.m3e_last_launch_count.argtypes = [vp]
     lib.m3e_last_error_string.restype = C.c_char_p
     lib.m3e_set_profiling.argtypes = [vp, C.c_int]
+    lib.m3e_stream_open.argtypes = [vp, C.POINTER(StreamParams)]
+    lib.m3e_stream_submit.argtypes = [vp, vp, C.c_int32, C.c_uint64, vp]
+    lib.m3e_stream_poll.argtypes = [vp, C.POINTER(StreamStatus)]
+    lib.m3e_stream_drain.argtypes = [vp, i64]
+    lib.m3e_stream_close.argtypes = [vp]
+    lib.m3e_stream_replay.argtypes = [vp, vp, vp, i64, C.c_double, C.c_uint64, vp, vp, vp, vp,
+                                      C.POINTER(ReplayStats)]
     lib.m3e_kernel_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     return lib
 
@@ -286,6 +316,58 @@ class Context:
         a, b = C.c_float(), C.c_float()
         _check(lib.m3e_kernel_times(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+
+    # ---------------------------------------------------------------- streaming
+
+    def stream_open(self, **params):
+        """``m3e_stream_open``; keyword arguments are fields of ``m3e_stream_params``."""
+        p = StreamParams()
+        p.size = C.sizeof(StreamParams)
+        for k, v in params.items():
+            setattr(p, k, v)
+        _check(lib.m3e_stream_open(self._h, C.byref(p)))
+
+    def stream_submit(self, packet: np.ndarray, tag: int, slot: Result) -> int:
+        """``m3e_stream_submit`` of one frame (int32 addresses); returns OK or EBUSY, raises otherwise."""
+        pk = np.ascontiguousarray(packet, dtype=np.int32)
+        rc = lib.m3e_stream_submit(self._h, pk.ctypes.data if pk.size else None, pk.size, tag, C.addressof(slot))
+        if rc not in (OK, EBUSY):
+            _check(rc)
+        return rc
+
+    def stream_poll(self) -> dict:
+        st = StreamStatus()
+        _check(lib.m3e_stream_poll(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in StreamStatus._fields_}
+
+    def stream_drain(self, timeout_ms: int = 10000) -> int:
+        """``m3e_stream_drain``; returns OK or ETIMEOUT."""
+        rc = lib.m3e_stream_drain(self._h, timeout_ms)
+        if rc not in (OK, ETIMEOUT):
+            _check(rc)
+        return rc
+
+    def stream_close(self) -> int:
+        return lib.m3e_stream_close(self._h)
+
+    def stream_replay(self, hits: np.ndarray, off: np.ndarray, rate_hz: float, seed: int = 5) -> dict:
+        """``m3e_stream_replay``: open-loop Poisson arrivals of a host CSR batch; per-frame decisions
+        and latencies (ns) plus the run's rates."""
+        h = np.ascontiguousarray(hits, dtype=np.int32)
+        o = np.ascontiguousarray(off, dtype=np.int64)
+        nf = o.size - 1
+        keep = np.zeros(max(nf, 1), np.uint8)
+        reason = np.zeros(max(nf, 1), np.uint8)
+        ls = np.zeros(max(nf, 1), np.int64)
+        la = np.zeros(max(nf, 1), np.int64)
+        st = ReplayStats()
+        _check(lib.m3e_stream_replay(self._h, h.ctypes.data, o.ctypes.data, nf, float(rate_hz), seed,
+                                     keep.ctypes.data, reason.ctypes.data, ls.ctypes.data, la.ctypes.data,
+                                     C.byref(st)))
+        out = {k: getattr(st, k) for k, _ in ReplayStats._fields_}
+        out.update(keep=keep[:nf], reason=reason[:nf], lat_submit_ns=ls[:nf], lat_arrival_ns=la[:nf])
+        return out
 
 
 class Graph:

@@ -60,3 +60,45 @@ def test_config_struct_layout_matches_header():
     body = txt[txt.index("typedef struct {\n  uint32_t size;"):txt.index("} m3e_config;")]
     decl = re.findall(r"(\w+)(?:\[\d+\])?\s*[,;]", body)
     assert [n for n in decl if n in names] == names
+
+
+def _c_layout(struct: str, fields: list[str], tmp_path) -> list[int]:
+    """sizeof and offsetof of a header struct, from a C program compiled here with gcc."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "m3e.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
+                           str(src), "-o", str(exe)])
+    return [int(x) for x in subprocess.check_output([str(exe)], text=True).split()]
+
+
+@pytest.mark.parametrize("name,struct", [("Result", "m3e_result"), ("StreamParams", "m3e_stream_params"),
+                                         ("StreamStatus", "m3e_stream_status"), ("ReplayStats", "m3e_replay_stats"),
+                                         ("Tuning", "m3e_tuning"), ("Config", "m3e_config")])
+def test_ctypes_mirrors_match_the_c_layout(name, struct, tmp_path):
+    import shutil
+    if not shutil.which("gcc") or not os.path.exists("/usr/local/cuda/include/cuda_runtime.h"):
+        pytest.skip("gcc or the CUDA headers are missing")
+    from paper_2206_11535_gb300 import m3e
+    cls = getattr(m3e, name)
+    fields = [f[0] for f in cls._fields_]
+    want = _c_layout(struct, fields, tmp_path)
+    got = [C.sizeof(cls)] + [getattr(cls, f).offset for f in fields]
+    assert got == want
+
+
+def test_stream_entry_points_check_arguments(lib):
+    from paper_2206_11535_gb300 import m3e
+    L = m3e.lib
+    slot = m3e.Result()
+    assert L.m3e_stream_submit(None, None, 0, 0, C.addressof(slot)) == m3e.EINVAL
+    assert L.m3e_stream_poll(None, None) == m3e.EINVAL
+    assert L.m3e_stream_drain(None, 0) == m3e.EINVAL
+    assert L.m3e_stream_close(None) == m3e.EINVAL
+    assert L.m3e_stream_open(None, None) == m3e.EINVAL
+    assert L.m3e_stream_replay(None, None, None, 0, 1.0, 0, None, None, None, None, None) == m3e.EINVAL

@@ -220,6 +220,20 @@ def test_stats_counters(ctx, m3e, ocfg, form):
     _, _, cnt = O.select_frames(ocfg, d["hits"], d["off"], 4, counts=True)
     assert abs(s["triplets"] - cnt[:, 3].sum()) <= 5
     assert abs(s["tracks"] - cnt[:, 4].sum()) <= 5
+    # binned work counts: the warp stage (every lane's share) and the CTA-per-frame
+    # form count the same phi windows and candidate triplets; the binned pairs are
+    # a subset of the oracle's brute-force pairs, and every selected triplet was a candidate
+    stp = m3e.new_stats()
+    ctx.select_frames_plain(*_dev(d), stats=stp)
+    torch.cuda.synchronize()
+    sp = m3e.stats_dict(stp)
+    for k in ("pair_tests", "triplet_tests", "triplets", "tracks", "energy_tests", "combos"):
+        assert s[k] == sp[k], (k, s[k], sp[k])
+    assert 0 < s["pair_tests"] <= cnt[:, 1].sum()
+    # candidate triplets = sum over layer-1 hits of (Phi01 partners x Phi12 partners),
+    # the oracle's count in FP64 (equal up to hits on a Phi-cut boundary)
+    assert abs(s["triplet_tests"] - cnt[:, 2].sum()) <= 1e-3 * cnt[:, 2].sum() + 5
+    assert s["triplets"] <= s["triplet_tests"]
 
 
 def test_c3_uneven_frames_sample(ctx, ocfg):
