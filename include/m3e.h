@@ -264,7 +264,7 @@ int m3e_select_frames_noalloc(m3e_ctx* ctx, const int32_t* d_hits, const int64_t
  *     frames in submission order.  One warp of it moves new descriptors into a
  *     device ring; each worker warp waits, with bounded back-off, for the frame
  *     of the ticket it drew, reads the hits over the host link and writes a
- *     completion word into a pinned completion ring.
+ *     completion word into a pinned completion queue, in completion order.
  *   - A library thread delivers completions into the caller's result slots,
  *     frees ring space in submission order and relaunches the resident kernel
  *     when it has exited while frames are waiting.
@@ -306,6 +306,8 @@ typedef struct {
   uint64_t submitted, completed, busy_refusals;
   uint64_t kernel_launches;  /* resident kernel launches so far */
   uint64_t heavy_frames;     /* frames run by the CTA-per-frame kernel */
+  uint64_t delivery_passes;  /* passes of the library thread that delivered results */
+  uint64_t tail_publications; /* stores of the descriptor tail seen by the GPU */
   int32_t kernel_running;    /* resident kernel currently on the GPU */
   int32_t failed;            /* a device wait expired: frames in flight were lost (M3E_ETIMEOUT) */
 } m3e_stream_status;
@@ -324,6 +326,17 @@ int m3e_stream_open(m3e_ctx* ctx, const m3e_stream_params* params);
 int m3e_stream_submit(m3e_ctx* ctx, const int32_t* h_packet, int32_t n_hits, uint64_t tag,
                       m3e_result* h_result_slot);
 
+/* Submit a CSR batch of host frames at once: frame f is h_hits[h_frame_off[f]
+ * .. h_frame_off[f+1]), its result slot h_results[f], its tag tags[f] (tags may
+ * be NULL: tag = f).  Frames are admitted in order until one does not fit; one
+ * lock, one clock reading (t_submit_ns) and one publication serve the whole
+ * batch, so a host that receives frames in bursts pays the fixed cost once.
+ * *n_admitted (may be NULL) receives the number admitted; returns M3E_OK when
+ * all were, M3E_EBUSY when only the first *n_admitted were (resubmit the rest
+ * later), M3E_EINVAL for bad sizes or NULL pointers (nothing admitted). */
+int m3e_stream_submit_many(m3e_ctx* ctx, const int32_t* h_hits, const int64_t* h_frame_off, int64_t n_frames,
+                           const uint64_t* tags, m3e_result* h_results, int64_t* n_admitted);
+
 /* Counters of the stream (no wait). */
 int m3e_stream_poll(m3e_ctx* ctx, m3e_stream_status* out);
 
@@ -340,15 +353,17 @@ typedef struct {
   double offered_hz;         /* arrival rate asked for */
   double sustained_hz;       /* frames / (last result time - first arrival time) */
   double submit_hz;          /* frames / (last submit time - first arrival time) */
-  uint64_t busy_retries;     /* submissions refused with M3E_EBUSY and retried */
+  uint64_t busy_retries;     /* submission calls not fully admitted (M3E_EBUSY), rest retried */
   uint64_t kernel_launches;
   int64_t duration_ns;
 } m3e_replay_stats;
 
 /* Latency harness: replay a CSR batch of host frames as an open-loop Poisson
  * arrival process of rate_hz (exponential gaps from a seeded counter-based
- * generator, splitmix64).  One submitting thread waits for each frame's arrival
- * time and submits it, retrying while the stream is busy.  Per frame it returns
+ * generator, splitmix64).  One submitting thread waits for the next arrival
+ * time and submits every frame that has arrived by then in one call (as
+ * m3e_stream_submit_many, at most 1024), retrying what the stream refused;
+ * below the host's per-call rate that is one frame per call.  Per frame it returns
  * keep and reason, the latency from submission to result (out_lat_submit_ns)
  * and from the scheduled arrival to result (out_lat_arrival_ns, which includes
  * any wait for admission).  Any output pointer may be NULL.  Waits at most

@@ -944,6 +944,18 @@ int m3e_stream_submit(m3e_ctx* x, const int32_t* h_packet, int32_t n_hits, uint6
   return stream_submit(x->stream, h_packet, n_hits, tag, h_result_slot);
 }
 
+int m3e_stream_submit_many(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_frame_off, int64_t n_frames,
+                           const uint64_t* tags, m3e_result* h_results, int64_t* n_admitted) {
+  if (n_admitted) *n_admitted = 0;
+  if (!x) return fail(M3E_EINVAL, "ctx is NULL");
+  if (!x->stream) {
+    DeviceGuard guard(x->device);
+    const int rc = stream_create(x->device, x->sms, x->dc, stream_base(x), nullptr, &x->stream);
+    if (rc) return rc;
+  }
+  return stream_submit_many(x->stream, h_hits, h_frame_off, n_frames, tags, h_results, n_admitted);
+}
+
 int m3e_stream_poll(m3e_ctx* x, m3e_stream_status* out) {
   if (!x || !out) return fail(M3E_EINVAL, "ctx or out is NULL");
   if (!x->stream) return fail(M3E_ESTATE, "stream not open");

@@ -112,6 +112,8 @@ struct StreamEngine;
 int stream_create(int device, int sms, const DevCfg& dc, const KParams& base, const m3e_stream_params* sp,
                   StreamEngine** out);
 int stream_submit(StreamEngine* e, const int32_t* pkt, int32_t n_hits, uint64_t tag, m3e_result* res);
+int stream_submit_many(StreamEngine* e, const int32_t* hits, const int64_t* off, int64_t n_frames,
+                       const uint64_t* tags, m3e_result* res, int64_t* admitted);
 int stream_poll(StreamEngine* e, m3e_stream_status* out);
 int stream_drain(StreamEngine* e, int64_t timeout_ms);
 int stream_destroy(StreamEngine* e);

@@ -13,9 +13,10 @@
 //           with bounded back-off for its slot, reads the hits from the host
 //           ring over the host link and runs the per-frame method (the fused
 //           warp stage), then writes a completion word {seq, reason, keep} into
-//           a pinned completion ring (release, system scope);
-//   host    the library thread delivers completion words into the caller's
-//           result slots and frees ring space in submission order.
+//           a pinned completion queue, in completion order (release, system
+//           scope);
+//   host    the library thread consumes the queue, delivers the results into
+//           the caller's slots and frees ring space in submission order.
 // Frames with more hits than the warp stage holds are batched by the library
 // thread to a CTA-per-frame kernel.  The resident kernel exits when idle or at
 // the end of its lifetime (and the thread relaunches it while frames wait);
@@ -71,10 +72,11 @@ struct StreamK {
   const int32_t* ring;            // device view of the host packet ring
   const HDesc* hdesc;             // device view of the host descriptor ring
   Control* ctl;                   // device view of the control block
-  unsigned long long* hcomp;      // device view of the host completion ring
+  unsigned long long* hcomp;      // device view of the host completion queue (completion order)
   DDesc* ddesc;                   // device descriptor ring
   unsigned long long* dseq;       // published sequence number of each device-ring slot
   unsigned long long* dstate;     // [0] tickets drawn in this launch, [1] stop ticket + 1 (0 = running)
+  unsigned long long* dcq;        // completions written so far (all launches): the queue's tail
   unsigned long long base;        // first ticket of this launch
   unsigned long long mask;        // slots - 1
   long long idle_ns, life_ns, wait_ns;
@@ -111,6 +113,9 @@ __device__ __forceinline__ unsigned ld_relaxed_sys(const unsigned* p) {
 __device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed_gpu(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -144,14 +149,27 @@ __device__ void feeder(const StreamK& K) {
     const long long now = now_ns();
     if (stop || now - t0 > K.life_ns) break;
     if (tail > pub && tail - pub <= K.mask + 1) {
-      for (unsigned long long i = pub + lane; i < tail; i += 32) {
-        const HDesc* h = K.hdesc + (i & K.mask);
-        DDesc d;
-        d.off = __ldcv(&h->off);
-        d.n = __ldcv(&h->n);
-        d.pad = 0;
-        K.ddesc[i & K.mask] = d;
-        st_release_gpu(&K.dseq[i & K.mask], i);
+      // groups of 128 descriptors, four per lane: the four 16-byte loads over the
+      // host link are in flight together, and one fence orders the group's
+      // device-ring writes before its sequence numbers (release pattern)
+      for (unsigned long long b = pub; b < tail; b += 128) {
+        int4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const unsigned long long i = b + j * 32 + lane;
+          v[j] = i < tail ? __ldcv(reinterpret_cast<const int4*>(K.hdesc + (i & K.mask))) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const unsigned long long i = b + j * 32 + lane;
+          if (i < tail) *reinterpret_cast<int4*>(K.ddesc + (i & K.mask)) = v[j];
+        }
+        __threadfence();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const unsigned long long i = b + j * 32 + lane;
+          if (i < tail) st_relaxed_gpu(&K.dseq[i & K.mask], i);
+        }
       }
       pub = tail;
       last = now;
@@ -221,7 +239,11 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     // CTA kernel); keep one conservatively should that ever change
     if (r == DEFERRED) r = M3E_HIT_OVERFLOW;
     g.sync();
-    if (g.leader()) st_release_sys(&K.hcomp[t & K.mask], completion_word(t, r));
+    // append to the completion queue: the host consumes it in order, O(1) per frame
+    if (g.leader()) {
+      const unsigned long long c = atomicAdd(K.dcq, 1ull);
+      st_release_sys(&K.hcomp[c & K.mask], completion_word(t, r));
+    }
   }
 }
 
@@ -314,6 +336,8 @@ struct StreamEngine {
   DDesc* ddesc = nullptr;
   unsigned long long* dseq = nullptr;
   unsigned long long* dstate = nullptr;
+  unsigned long long* dcq = nullptr;
+  uint64_t cq_head = 0;           // next completion-queue entry to consume (library thread)
   cudaStream_t rs = nullptr, hs = nullptr;
   cudaEvent_t re = nullptr, he = nullptr;
   int grid = 1;
@@ -331,33 +355,69 @@ struct StreamEngine {
   SpinLock lock;
   uint64_t gseq = 0, lseq = 0;
   int64_t wpos = 0;
+  uint64_t low_seen = 0;          // last values of low and rpos read by the producer: re-read
+  int64_t rpos_seen = 0;          // only when the ring looks full (they only grow)
   std::vector<HeavyItem> heavy_pending;
-  std::atomic<uint64_t> gseq_pub{0}, lseq_pub{0};
-  // consumer side
-  std::atomic<uint64_t> low{0};   // every frame below is delivered and released
-  std::atomic<int64_t> rpos{0};   // ring words below are free
-  uint64_t lscan = 0;
+  // written by the producer, read by the library thread (own cache line)
+  alignas(64) std::atomic<uint64_t> gseq_pub{0};
+  std::atomic<uint64_t> lseq_pub{0};
+  std::atomic<uint64_t> heavy_n{0};     // frames in heavy_pending
+  std::atomic<bool> asleep{false};      // library thread asleep; set and cleared under the lock
+  // written by the library thread, read by the producer (own cache line)
+  alignas(64) std::atomic<uint64_t> low{0};   // every frame below is delivered and released
+  std::atomic<int64_t> rpos{0};               // ring words below are free
+  alignas(64) uint64_t lscan = 0;
+  uint64_t tail_pub = 0;          // last tail the library thread stored into the control block
   bool rk_running = false, hk_running = false;
   uint64_t rk_base = 0;
   int hk_count = 0;
   // counters and flags
   std::atomic<uint64_t> completed{0}, busy{0}, launches{0}, heavy{0};
+  std::atomic<uint64_t> passes_delivering{0}, tail_stores{0};
   std::atomic<bool> failed{false}, quit{false}, running_flag{false};
-  std::atomic<int> sleeping{0};
   std::mutex mu;
   std::condition_variable cv;
   std::thread th;
 
-  void deliver(uint64_t g, int keep, int reason, int err) {
+  // t_done: the delivery time (read once per pass of the library thread)
+  void deliver(uint64_t g, int keep, int reason, int err, int64_t t_done = -1) {
     Slot& s = slots[g & mask];
     m3e_result* r = s.res;
     r->keep = (uint8_t)keep;
     r->reason = (uint8_t)reason;
     r->err = err ? err : (reason == M3E_ERR_BADHIT ? M3E_EBADHIT : M3E_OK);
-    r->t_done_ns = (uint64_t)host_ns();
+    r->t_done_ns = (uint64_t)(t_done >= 0 ? t_done : host_ns());
     __atomic_store_n(&r->done, 1u, __ATOMIC_RELEASE);
-    s.state.store(2, std::memory_order_release);
-    completed.fetch_add(1, std::memory_order_relaxed);
+    s.state.store(2, std::memory_order_relaxed);  // read by this thread only
+    completed.store(completed.load(std::memory_order_relaxed) + 1, std::memory_order_relaxed);  // one writer
+  }
+
+  // Deliveries of the completion queue, in batches: every field of the batch,
+  // one release fence, then the done flags (one fence per batch, not per frame).
+  static constexpr int DB = 64;
+  uint64_t db_g[DB];
+  unsigned long long db_w[DB];
+  int db_n = 0;
+  void flush_deliveries() {
+    if (!db_n) return;
+    const uint64_t t = (uint64_t)host_ns();
+    for (int i = 0; i < db_n; ++i) {
+      m3e_result* r = slots[db_g[i] & mask].res;
+      const int reason = (int)((db_w[i] >> 8) & 255);
+      r->keep = (uint8_t)(db_w[i] & 1);
+      r->reason = (uint8_t)reason;
+      r->err = reason == M3E_ERR_BADHIT ? M3E_EBADHIT : M3E_OK;
+      r->t_done_ns = t;
+    }
+    std::atomic_thread_fence(std::memory_order_release);
+    for (int i = 0; i < db_n; ++i) {
+      Slot& sl = slots[db_g[i] & mask];
+      __atomic_store_n(&sl.res->done, 1u, __ATOMIC_RELAXED);
+      sl.state.store(2, std::memory_order_relaxed);
+    }
+    completed.store(completed.load(std::memory_order_relaxed) + (uint64_t)db_n, std::memory_order_relaxed);
+    db_n = 0;
+    publish_tail();  // keep the feeder supplied during long passes
   }
 
   cudaError_t launch_resident(uint64_t b) {
@@ -370,6 +430,7 @@ struct StreamEngine {
     k.ddesc = ddesc;
     k.dseq = dseq;
     k.dstate = dstate;
+    k.dcq = dcq;
     k.base = b;
     k.mask = mask;
     k.idle_ns = (long long)prm.idle_us * 1000LL;
@@ -395,23 +456,36 @@ struct StreamEngine {
     return cudaEventRecord(he, hs);
   }
 
-  // Light completions written by the resident kernel, delivered in any order.
+  // Light completions written by the resident kernel, consumed from the
+  // completion queue in completion order (an entry is written once its index is
+  // drawn; the consumer clears it before delivering, so that it is empty again
+  // before the queue wraps: at most `slots` frames are undelivered).  With
+  // fail_rest, every light frame still in flight afterwards is failed.
   bool scan_light(bool fail_rest) {
     bool any = false;
-    const uint64_t lp = lseq_pub.load(std::memory_order_acquire);
-    for (uint64_t l = lscan; l < lp; ++l) {
-      if (ldone[l & mask]) continue;
-      const unsigned long long wv = __atomic_load_n(&hcomp[l & mask], __ATOMIC_ACQUIRE);
-      if ((wv >> 16) == (l & 0xffffffffffffULL)) {
-        deliver(lmap[l & mask], (int)(wv & 1), (int)((wv >> 8) & 255), 0);
-      } else if (fail_rest) {
-        deliver(lmap[l & mask], 1, M3E_ERR_BADHIT, M3E_ETIMEOUT);
-      } else {
-        continue;
-      }
+    for (;;) {
+      unsigned long long* e = &hcomp[cq_head & mask];
+      const unsigned long long wv = __atomic_load_n(e, __ATOMIC_ACQUIRE);
+      if (wv == ~0ULL) break;
+      __atomic_store_n(e, ~0ULL, __ATOMIC_RELAXED);
+      ++cq_head;
+      const uint64_t l = wv >> 16;
+      db_g[db_n] = lmap[l & mask];
+      db_w[db_n] = wv;
+      if (++db_n == DB) flush_deliveries();
       ldone[l & mask] = 1;
       any = true;
     }
+    flush_deliveries();
+    if (any) passes_delivering.fetch_add(1, std::memory_order_relaxed);
+    const uint64_t lp = lseq_pub.load(std::memory_order_acquire);
+    if (fail_rest)
+      for (uint64_t l = lscan; l < lp; ++l)
+        if (!ldone[l & mask]) {
+          deliver(lmap[l & mask], 1, M3E_ERR_BADHIT, M3E_ETIMEOUT);
+          ldone[l & mask] = 1;
+          any = true;
+        }
     while (lscan < lp && ldone[lscan & mask]) ldone[lscan++ & mask] = 0;
     return any;
   }
@@ -423,6 +497,7 @@ struct StreamEngine {
     std::vector<HeavyItem> left;
     lock.lock();
     left.swap(heavy_pending);
+    heavy_n.store(0, std::memory_order_relaxed);
     lock.unlock();
     for (const HeavyItem& h : left) deliver(h.gseq, 1, M3E_ERR_BADHIT, M3E_ETIMEOUT);
   }
@@ -440,10 +515,26 @@ struct StreamEngine {
     low.store(lo, std::memory_order_release);
   }
 
+  // Make the light frames submitted so far visible to the resident kernel.  The
+  // library thread publishes (one store of the polled tail word for any number
+  // of submissions), so that the submitting thread never writes the word the
+  // GPU is polling.
+  void publish_tail() {
+    const uint64_t lp = lseq_pub.load(std::memory_order_acquire);
+    if (lp != tail_pub) {
+      __atomic_store_n(&ctl->tail, (unsigned long long)lp, __ATOMIC_RELEASE);
+      tail_pub = lp;
+      tail_stores.store(tail_stores.load(std::memory_order_relaxed) + 1, std::memory_order_relaxed);
+    }
+  }
+
   void run() {
     cudaSetDevice(device);
+    int64_t idle_since = -1;
     for (;;) {
+      publish_tail();
       bool progress = scan_light(false);
+      publish_tail();
       const uint64_t lp = lseq_pub.load(std::memory_order_acquire);
       // resident kernel: exited?  relaunch while light frames wait
       if (rk_running && cudaEventQuery(re) != cudaErrorNotReady) {
@@ -473,13 +564,14 @@ struct StreamEngine {
         hk_running = false;
         progress = true;
       }
-      if (!hk_running && !failed.load() && !quit.load()) {
+      if (!hk_running && !failed.load() && !quit.load() && heavy_n.load(std::memory_order_relaxed)) {
         int n = 0;
         lock.lock();
         if (!heavy_pending.empty()) {
           n = (int)std::min<size_t>(heavy_pending.size(), (size_t)heavy_cap);
           memcpy(hitems, heavy_pending.data(), sizeof(HeavyItem) * n);
           heavy_pending.erase(heavy_pending.begin(), heavy_pending.begin() + n);
+          heavy_n.fetch_sub((uint64_t)n, std::memory_order_relaxed);
         }
         lock.unlock();
         if (n) {
@@ -498,78 +590,111 @@ struct StreamEngine {
       if (none_running && (failed.load() || quit.load())) fail_pending();
       release_in_order();
       if (quit.load() && none_running) break;
-      if (!progress) {
-        if (low.load() == gseq_pub.load()) {
-          // nothing in flight: sleep until a submission (the resident kernel
-          // exits by itself when idle; its exit is noticed on wake-up or timeout)
-          std::unique_lock<std::mutex> lk(mu);
-          sleeping.store(1);
-          std::atomic_thread_fence(std::memory_order_seq_cst);
-          if (low.load() == gseq_pub.load() && !quit.load())
-            cv.wait_for(lk, std::chrono::milliseconds(rk_running || hk_running ? 1 : 20));
-          sleeping.store(0);
-        } else {
+      if (progress || low.load() != gseq_pub.load()) {
+        idle_since = -1;
+        if (!progress)
           for (int i = 0; i < 16; ++i) cpu_relax();
-        }
+        continue;
+      }
+      // nothing in flight: keep spinning for a while (frames at a steady rate
+      // should not pay a wake-up), then sleep until a submission wakes us.  The
+      // decision to sleep and the producer's check of it are both made under the
+      // producer lock, so a submission cannot slip between them.
+      const int64_t now = host_ns();
+      if (idle_since < 0) idle_since = now;
+      if (now - idle_since < 200000) {
+        for (int i = 0; i < 64; ++i) cpu_relax();
+        continue;
+      }
+      lock.lock();
+      const bool go = gseq == low.load(std::memory_order_relaxed) && !quit.load();
+      if (go) asleep.store(true, std::memory_order_relaxed);
+      lock.unlock();
+      if (go) {
+        // the resident kernel exits by itself when idle; its exit is noticed on
+        // wake-up or on the timeout
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait_for(lk, std::chrono::milliseconds(rk_running || hk_running ? 1 : 20),
+                    [&] { return !asleep.load() || quit.load(); });
+        lock.lock();
+        asleep.store(false, std::memory_order_relaxed);
+        lock.unlock();
       }
     }
+  }
+
+  // Admit frames first .. first + count - 1 of a CSR batch (hits of frame f at
+  // hits[off[f] .. off[f + 1]), result slot res[f - first], tag tags[f - first]
+  // or tag0 + (f - first)) in order, until one does not fit.  One lock, one clock
+  // read and one publication for the whole range.  Returns the number admitted.
+  int64_t submit_range(const int32_t* hits, const int64_t* off, int64_t first, int64_t count, const uint64_t* tags,
+                       uint64_t tag0, m3e_result* res) {
+    lock.lock();
+    const uint64_t t_submit = (uint64_t)host_ns();
+    const uint64_t g0 = gseq, l0 = lseq;
+    int64_t k = 0;
+    bool heavy_added = false;
+    for (; k < count; ++k) {
+      const int64_t f = first + k;
+      const int64_t n = off[f + 1] - off[f];
+      const uint64_t g = gseq;
+      if (g - low_seen >= S && g - (low_seen = low.load(std::memory_order_acquire)) >= S) break;
+      const int64_t rem = W - (wpos % W);
+      const int64_t start = n > rem ? wpos + rem : wpos;
+      const int64_t end = start + n;
+      if (end - rpos_seen > W && end - (rpos_seen = rpos.load(std::memory_order_acquire)) > W) break;
+      wpos = end;
+      const int64_t o = start % W;
+      if (n) memcpy(ring + o, hits + off[f], sizeof(int32_t) * (size_t)n);
+      m3e_result* r = res + k;
+      r->keep = 0;
+      r->reason = 0;
+      r->err = 0;
+      r->tag = tags ? tags[k] : tag0 + (uint64_t)k;
+      r->t_done_ns = 0;
+      r->t_submit_ns = t_submit;
+      __atomic_store_n(&r->done, 0u, __ATOMIC_RELAXED);
+      Slot& sl = slots[g & mask];
+      sl.res = r;
+      sl.word_end = end;
+      sl.state.store(1, std::memory_order_relaxed);
+      gseq = g + 1;
+      if (n <= W_HITS) {
+        const uint64_t l = lseq;
+        hdesc[l & mask].off = o;
+        hdesc[l & mask].n = (int)n;
+        lmap[l & mask] = g;
+        lseq = l + 1;
+      } else {
+        heavy_pending.push_back(HeavyItem{o, (int)n, 0, g});
+        heavy_added = true;
+      }
+    }
+    if (heavy_added) heavy_n.store(heavy_pending.size(), std::memory_order_relaxed);
+    if (gseq != g0) gseq_pub.store(gseq, std::memory_order_release);
+    if (lseq != l0) lseq_pub.store(lseq, std::memory_order_release);
+    // the library thread publishes the tail while it runs; asleep, it is woken
+    // and the frames are published here (the thread decides to sleep under this
+    // lock, so the check cannot miss them)
+    const bool wake = k > 0 && asleep.load(std::memory_order_relaxed);
+    if (wake) {
+      asleep.store(false, std::memory_order_relaxed);
+      __atomic_store_n(&ctl->tail, (unsigned long long)lseq, __ATOMIC_RELEASE);
+    }
+    lock.unlock();
+    if (k < count) busy.fetch_add(1, std::memory_order_relaxed);
+    if (wake) {
+      std::lock_guard<std::mutex> lk(mu);
+      cv.notify_one();
+    }
+    return k;
   }
 
   int submit(const int32_t* pkt, int32_t n, uint64_t tag, m3e_result* res) {
     if (failed.load(std::memory_order_relaxed)) return m3e_set_error(M3E_ETIMEOUT, "stream has failed");
     if (quit.load(std::memory_order_relaxed)) return m3e_set_error(M3E_ESTATE, "stream is closing");
-    lock.lock();
-    const uint64_t g = gseq;
-    if (g - low.load(std::memory_order_acquire) >= S) {
-      lock.unlock();
-      busy.fetch_add(1, std::memory_order_relaxed);
-      return M3E_EBUSY;
-    }
-    const int64_t rem = W - (wpos % W);
-    const int64_t start = n > rem ? wpos + rem : wpos;
-    const int64_t end = start + n;
-    if (end - rpos.load(std::memory_order_acquire) > W) {
-      lock.unlock();
-      busy.fetch_add(1, std::memory_order_relaxed);
-      return M3E_EBUSY;
-    }
-    wpos = end;
-    const int64_t off = start % W;
-    if (n) memcpy(ring + off, pkt, sizeof(int32_t) * (size_t)n);
-    res->keep = 0;
-    res->reason = 0;
-    res->err = 0;
-    res->tag = tag;
-    res->t_done_ns = 0;
-    res->t_submit_ns = (uint64_t)host_ns();
-    __atomic_store_n(&res->done, 0u, __ATOMIC_RELAXED);
-    Slot& s = slots[g & mask];
-    s.res = res;
-    s.word_end = end;
-    s.state.store(1, std::memory_order_relaxed);
-    gseq = g + 1;
-    if (n <= W_HITS) {
-      const uint64_t l = lseq;
-      hdesc[l & mask].off = off;
-      hdesc[l & mask].n = n;
-      lmap[l & mask] = g;
-      lseq = l + 1;
-      gseq_pub.store(g + 1, std::memory_order_release);
-      lseq_pub.store(l + 1, std::memory_order_release);
-      __atomic_store_n(&ctl->tail, (unsigned long long)(l + 1), __ATOMIC_RELEASE);
-    } else {
-      heavy_pending.push_back(HeavyItem{off, n, 0, g});
-      gseq_pub.store(g + 1, std::memory_order_release);
-    }
-    lock.unlock();
-    // pairs with the library thread's store of `sleeping` before its last look
-    // at gseq_pub: one of the two sides sees the other's write
-    std::atomic_thread_fence(std::memory_order_seq_cst);
-    if (sleeping.load()) {
-      std::lock_guard<std::mutex> lk(mu);
-      cv.notify_one();
-    }
-    return M3E_OK;
+    const int64_t off[2] = {0, n};
+    return submit_range(pkt, off, 0, 1, nullptr, tag, res) == 1 ? M3E_OK : M3E_EBUSY;
   }
 
   int drain(int64_t timeout_ms) {
@@ -593,6 +718,7 @@ struct StreamEngine {
     cudaFree(ddesc);
     cudaFree(dseq);
     cudaFree(dstate);
+    cudaFree(dcq);
     if (rs) cudaStreamDestroy(rs);
     if (hs) cudaStreamDestroy(hs);
     if (re) cudaEventDestroy(re);
@@ -674,12 +800,14 @@ int stream_create(int device, int sms, const DevCfg& dc, const KParams& base, co
   S_TRY(host_mapped(&E->hitems, &E->d_hitems, sizeof(HeavyItem) * E->heavy_cap));
   S_TRY(host_mapped(&E->hres, &E->d_hres, sizeof(unsigned short) * E->heavy_cap));
   memset(E->ctl, 0, sizeof(Control));
-  memset(E->hcomp, 0xff, sizeof(unsigned long long) * E->S);  // no valid sequence number
+  memset(E->hcomp, 0xff, sizeof(unsigned long long) * E->S);  // all entries empty
   S_TRY(cudaMalloc(&E->ddesc, sizeof(DDesc) * E->S));
   S_TRY(cudaMalloc(&E->dseq, sizeof(unsigned long long) * E->S));
   S_TRY(cudaMalloc(&E->dstate, 2 * sizeof(unsigned long long)));
+  S_TRY(cudaMalloc(&E->dcq, sizeof(unsigned long long)));
   S_TRY(cudaStreamCreateWithFlags(&E->rs, cudaStreamNonBlocking));
   S_TRY(cudaMemsetAsync(E->dseq, 0xff, sizeof(unsigned long long) * E->S, E->rs));
+  S_TRY(cudaMemsetAsync(E->dcq, 0, sizeof(unsigned long long), E->rs));
   S_TRY(cudaStreamCreateWithFlags(&E->hs, cudaStreamNonBlocking));
   S_TRY(cudaEventCreateWithFlags(&E->re, cudaEventDisableTiming));
   S_TRY(cudaEventCreateWithFlags(&E->he, cudaEventDisableTiming));
@@ -704,6 +832,22 @@ int stream_submit(StreamEngine* E, const int32_t* pkt, int32_t n, uint64_t tag, 
   return E->submit(pkt, n, tag, res);
 }
 
+int stream_submit_many(StreamEngine* E, const int32_t* hits, const int64_t* off, int64_t n_frames,
+                       const uint64_t* tags, m3e_result* res, int64_t* admitted) {
+  if (admitted) *admitted = 0;
+  if (n_frames < 0 || (n_frames > 0 && (!off || !res))) return m3e_set_error(M3E_EINVAL, "submit_many: NULL arguments");
+  for (int64_t f = 0; f < n_frames; ++f) {
+    const int64_t n = off[f + 1] - off[f];
+    if (n < 0 || n > E->W || n > 0x7fffffff) return m3e_set_error(M3E_EINVAL, "submit_many: frame %lld has a bad size", (long long)f);
+    if (n > 0 && !hits) return m3e_set_error(M3E_EINVAL, "submit_many: hits is NULL");
+  }
+  if (E->failed.load(std::memory_order_relaxed)) return m3e_set_error(M3E_ETIMEOUT, "stream has failed");
+  if (E->quit.load(std::memory_order_relaxed)) return m3e_set_error(M3E_ESTATE, "stream is closing");
+  const int64_t k = n_frames ? E->submit_range(hits, off, 0, n_frames, tags, 0, res) : 0;
+  if (admitted) *admitted = k;
+  return k == n_frames ? M3E_OK : M3E_EBUSY;
+}
+
 int stream_poll(StreamEngine* E, m3e_stream_status* o) {
   o->submitted = E->gseq_pub.load();
   o->completed = E->completed.load();
@@ -711,6 +855,8 @@ int stream_poll(StreamEngine* E, m3e_stream_status* o) {
   o->kernel_launches = E->launches.load();
   o->heavy_frames = E->heavy.load();
   o->kernel_running = E->running_flag.load() ? 1 : 0;
+  o->delivery_passes = E->passes_delivering.load();
+  o->tail_publications = E->tail_stores.load();
   o->failed = E->failed.load() ? 1 : 0;
   return M3E_OK;
 }
@@ -777,17 +923,21 @@ int stream_replay(StreamEngine* E, const int32_t* hits, const int64_t* off, int6
   uint64_t retries = 0;
   const int64_t t0 = host_ns() + 2000000;  // start 2 ms from now
   int64_t last_submit = t0;
-  for (int64_t f = 0; f < nf; ++f) {
-    const int64_t due = t0 + arr[f];
-    while (host_ns() < due) cpu_relax();
-    for (;;) {
-      const int rc = E->submit(hits + off[f], (int32_t)(off[f + 1] - off[f]), (uint64_t)f, &res[f]);
-      if (rc == M3E_OK) break;
-      if (rc != M3E_EBUSY) return bail(rc);
-      ++retries;
+  // every frame whose arrival time has come is submitted in one call (at most
+  // 1024): below the host's per-call rate that is one frame per call
+  for (int64_t f = 0; f < nf;) {
+    int64_t now = host_ns();
+    while (now < t0 + arr[f]) {
       cpu_relax();
+      now = host_ns();
     }
-    submitted = f + 1;
+    int64_t e = f + 1;
+    while (e < nf && e - f < 1024 && t0 + arr[e] <= now) ++e;
+    if (E->failed.load(std::memory_order_relaxed)) return bail(m3e_set_error(M3E_ETIMEOUT, "stream has failed"));
+    const int64_t k = E->submit_range(hits, off, f, e - f, nullptr, (uint64_t)f, res + f);
+    if (k < e - f) ++retries;
+    f += k;
+    submitted = f;
   }
   last_submit = host_ns();
   if (!settle(30000)) return bail(m3e_set_error(M3E_ETIMEOUT, "replay: results missing 30 s after the last arrival"));

@@ -74,7 +74,8 @@ class StreamParams(C.Structure):
 
 class StreamStatus(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("busy_refusals", C.c_uint64),
-                ("kernel_launches", C.c_uint64), ("heavy_frames", C.c_uint64), ("kernel_running", C.c_int32),
+                ("kernel_launches", C.c_uint64), ("heavy_frames", C.c_uint64), ("delivery_passes", C.c_uint64),
+                ("tail_publications", C.c_uint64), ("kernel_running", C.c_int32),
                 ("failed", C.c_int32)]
 
 
@@ -109,6 +110,7 @@ def _load(path: str = LIB_PATH):
     lib.m3e_set_profiling.argtypes = [vp, C.c_int]
     lib.m3e_stream_open.argtypes = [vp, C.POINTER(StreamParams)]
     lib.m3e_stream_submit.argtypes = [vp, vp, C.c_int32, C.c_uint64, vp]
+    lib.m3e_stream_submit_many.argtypes = [vp, vp, vp, i64, vp, vp, C.POINTER(C.c_int64)]
     lib.m3e_stream_poll.argtypes = [vp, C.POINTER(StreamStatus)]
     lib.m3e_stream_drain.argtypes = [vp, i64]
     lib.m3e_stream_close.argtypes = [vp]
@@ -335,6 +337,19 @@ class Context:
         if rc not in (OK, EBUSY):
             _check(rc)
         return rc
+
+    def stream_submit_many(self, hits: np.ndarray, off: np.ndarray, slots, tags: np.ndarray | None = None) -> int:
+        """``m3e_stream_submit_many`` of a host CSR batch into ``slots`` (a ctypes array of
+        Result with one slot per frame); returns the number admitted."""
+        h = np.ascontiguousarray(hits, dtype=np.int32)
+        o = np.ascontiguousarray(off, dtype=np.int64)
+        t = None if tags is None else np.ascontiguousarray(tags, dtype=np.uint64)
+        n = C.c_int64()
+        rc = lib.m3e_stream_submit_many(self._h, h.ctypes.data if h.size else None, o.ctypes.data, o.size - 1,
+                                        None if t is None else t.ctypes.data, C.addressof(slots), C.byref(n))
+        if rc not in (OK, EBUSY):
+            _check(rc)
+        return n.value
 
     def stream_poll(self) -> dict:
         st = StreamStatus()

@@ -1,6 +1,7 @@
 """Streaming selection (m3e_stream_*) on the GPU: every frame's decision equals the
 batch selection's, alone and among others; the bounded device waits end in a
 reported error, not a hang; admission refuses what does not fit."""
+import ctypes as C
 import time
 
 import numpy as np
@@ -183,3 +184,39 @@ def test_stream_admission(m3e, cfg):
         rep = ctx.stream_replay(h2, o2, rate_hz=1.0e7, seed=3)
         np.testing.assert_array_equal(rep["reason"], reason[keep_idx])
         assert rep["busy_retries"] > 0
+
+
+def test_stream_submit_many(m3e, cfg):
+    """Batched submission: chunks of a CSR batch admitted in order (a prefix when the
+    slots run out), tags and decisions as for single submissions."""
+    hits, off = _mixed_batch(cfg, n=3000)
+    nf = off.size - 1
+    with m3e.Context(cfg, 0) as ctx:
+        keep, reason = _batch_reference(m3e, ctx, hits, off)
+        ctx.stream_open(slots=1024)
+        res = (m3e.Result * nf)()
+        tags = np.arange(nf, dtype=np.uint64) * 3 + 7
+        f = 0
+        partial = 0
+        while f < nf:
+            e = min(nf, f + 700)
+            sub_off = off[f:e + 1] - off[f]
+            slot0 = m3e.Result.from_buffer(res, f * C.sizeof(m3e.Result))
+            k = ctx.stream_submit_many(hits[off[f]:off[e]], sub_off, slot0, tags[f:e])
+            assert 0 <= k <= e - f
+            partial += k < e - f
+            f += k
+            if k == 0:
+                time.sleep(1e-4)
+        assert ctx.stream_drain(30000) == m3e.OK
+        np.testing.assert_array_equal(np.array([r.reason for r in res], np.uint8), reason)
+        np.testing.assert_array_equal(np.array([r.keep for r in res], np.uint8), keep)
+        assert [r.tag for r in res] == [int(t) for t in tags]
+        # a full slot ring admits a prefix only
+        ctx.stream_close()
+        ctx.stream_open(slots=8)
+        res2 = (m3e.Result * 64)()
+        k = ctx.stream_submit_many(hits[:off[64]], off[:65], res2)
+        assert 1 <= k <= 8
+        assert ctx.stream_drain(10000) == m3e.OK
+        assert all(res2[i].done == 1 and res2[i].tag == i and res2[i].reason == reason[i] for i in range(k))
