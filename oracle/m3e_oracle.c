@@ -797,3 +797,87 @@ int orc_select_frames(const orc_config* c, const int32_t* hits, const int64_t* o
   for (int t = 0; t < n_threads; t++) { pthread_join(th[t], NULL); rc |= jobs[t].rc; }
   return rc;
 }
+
+/* ------------------------------------------------------------------ alignment and fit chi2 */
+
+/* R = Rz(wz) Ry(wy) Rx(wx), row-major. */
+static void rotation(const double* w, double* R) {
+  const double cx = cos(w[0]), sx = sin(w[0]), cy = cos(w[1]), sy = sin(w[1]), cz = cos(w[2]), sz = sin(w[2]);
+  const double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
+  const double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+  const double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
+  double T[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      T[3 * i + j] = 0;
+      for (int k = 0; k < 3; k++) T[3 * i + j] += Ry[3 * i + k] * Rx[3 * k + j];
+    }
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      R[3 * i + j] = 0;
+      for (int k = 0; k < 3; k++) R[3 * i + j] += Rz[3 * i + k] * T[3 * k + j];
+    }
+}
+
+void orc_align_point(const double* p6, const double* xn, double* x) {
+  double R[9];
+  rotation(p6 + 3, R);
+  for (int i = 0; i < 3; i++) x[i] = R[3 * i] * xn[0] + R[3 * i + 1] * xn[1] + R[3 * i + 2] * xn[2] + p6[i];
+}
+
+static double fit_chi2_one(const orc_config* c, const int32_t* hits, int64_t n_hits, const int32_t* q,
+                           const double* params) {
+  double h[12];
+  for (int L = 0; L < 4; L++) {
+    orc_hit d;
+    if (q[L] < 0 || q[L] >= n_hits || orc_decode(c, (uint32_t)hits[q[L]], &d) != 0 || d.layer != L) return NAN;
+    const double xn[3] = {d.x, d.y, d.z};
+    orc_align_point(params + 6 * L, xn, h + 3 * L);
+  }
+  double out[4];
+  if (orc_fit_track_positions(c, h, out) != 0 || !isfinite(out[3])) return NAN;
+  return out[3];
+}
+
+typedef struct {
+  const orc_config* c;
+  const int32_t* hits;
+  int64_t n_hits;
+  const int32_t* cand;
+  int64_t k0, k1;
+  const double* params;
+  double* chi2;
+  int64_t n_ok;
+} orc_fit_job;
+
+static void* run_fit_job(void* p) {
+  orc_fit_job* j = (orc_fit_job*)p;
+  for (int64_t k = j->k0; k < j->k1; k++) {
+    j->chi2[k] = fit_chi2_one(j->c, j->hits, j->n_hits, j->cand + 4 * k, j->params);
+    j->n_ok += isfinite(j->chi2[k]);
+  }
+  return NULL;
+}
+
+int64_t orc_fit_chi2(const orc_config* c, const int32_t* hits, int64_t n_hits, const int32_t* cand, int64_t n_cand,
+                     const double* params, double* chi2, int32_t n_threads) {
+  orc_config cs = *c;
+  cs.field_scale = c->field_scale * params[24];
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  orc_fit_job jobs[256];
+  for (int t = 0; t < n_threads; t++) {
+    jobs[t].c = &cs; jobs[t].hits = hits; jobs[t].n_hits = n_hits; jobs[t].cand = cand;
+    jobs[t].k0 = n_cand * t / n_threads; jobs[t].k1 = n_cand * (t + 1) / n_threads;
+    jobs[t].params = params; jobs[t].chi2 = chi2; jobs[t].n_ok = 0;
+    if (n_threads > 1) pthread_create(&th[t], NULL, run_fit_job, &jobs[t]);
+    else run_fit_job(&jobs[t]);
+  }
+  int64_t n_ok = 0;
+  for (int t = 0; t < n_threads; t++) {
+    if (n_threads > 1) pthread_join(th[t], NULL);
+    n_ok += jobs[t].n_ok;
+  }
+  return n_ok;
+}

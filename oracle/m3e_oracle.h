@@ -106,6 +106,22 @@ int  orc_fit_track_positions(const orc_config* c, const double* h /* 4 x 3 */, d
 int  orc_fit_triplet_exact(const orc_config* c, const double* ha, const double* hb, const double* hc,
                            int mid_layer, double r_lo, double r_hi, double* R_out);
 
+/* ------------------------------------------------------------------ alignment
+ * Rigid alignment of the four layers (the detector model of the track fit,
+ * Sec. "Track Reconstruction", with each cylinder displaced): the hit measured at
+ * nominal position x_nom on layer L sits at R(w_L) x_nom + d_L in the global
+ * frame, R(w) = Rz(wz) Ry(wy) Rx(wx) (rotations about the global axes through the
+ * origin, x first), params[6L .. 6L+5] = dx, dy, dz [mm], wx, wy, wz [rad].
+ * params[24] scales the field (B * field_scale * params[24]). */
+void orc_align_point(const double* p6, const double* x_nom, double* x);
+/* chi2 of each frozen candidate: cand[4k .. 4k+3] are global indices into hits of a
+ * layer-0, -1, -2, -3 hit; the chi2 of the track fit (global chi2 at the mean
+ * curvature, as for a selected track) at the given alignment.  chi2[k] = NaN when a
+ * hit is invalid, on the wrong layer, or a fit fails.  Threads over candidate
+ * ranges.  Returns the number of finite chi2. */
+int64_t orc_fit_chi2(const orc_config* c, const int32_t* hits, int64_t n_hits, const int32_t* cand, int64_t n_cand,
+                     const double* params /* 25 */, double* chi2, int32_t n_threads);
+
 #ifdef __cplusplus
 }
 #endif

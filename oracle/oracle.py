@@ -107,6 +107,10 @@ def lib():
         _lib.orc_select_frames.argtypes = [P(Config), P(C.c_int32), P(C.c_int64), C.c_int64, P(C.c_uint8),
                                            P(C.c_uint8), C.c_int32, P(C.c_int64)]
         _lib.orc_fit_track_positions.argtypes = [P(Config), P(C.c_double), P(C.c_double)]
+        _lib.orc_align_point.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double)]
+        _lib.orc_fit_chi2.argtypes = [P(Config), P(C.c_int32), C.c_int64, P(C.c_int32), C.c_int64, P(C.c_double),
+                                      P(C.c_double), C.c_int32]
+        _lib.orc_fit_chi2.restype = C.c_int64
         _lib.orc_fit_triplet_exact.argtypes = [P(Config), P(C.c_double), P(C.c_double), P(C.c_double), C.c_int,
                                                C.c_double, C.c_double, P(C.c_double)]
     return _lib
@@ -242,3 +246,58 @@ def select_frames(c: Config, hits, off, n_threads: int = 1, counts: bool = False
     if counts:
         return keep[:nf], reason[:nf], cnt[:nf]
     return keep[:nf], reason[:nf]
+
+
+# ---------------------------------------------------------------- alignment and the fit gradient
+
+N_PARAMS = 25  # 4 layers x (dx, dy, dz [mm], wx, wy, wz [rad]) and the field scale
+
+
+def nominal_params() -> np.ndarray:
+    p = np.zeros(N_PARAMS)
+    p[24] = 1.0
+    return p
+
+
+def align_point(p6, x_nom) -> np.ndarray:
+    """R(w) x_nom + d for one layer's params (dx, dy, dz, wx, wy, wz), R = Rz Ry Rx."""
+    (_, pa), (_, pb), o = _dp(p6), _dp(x_nom), np.zeros(3)
+    lib().orc_align_point(pa, pb, o.ctypes.data_as(C.POINTER(C.c_double)))
+    return o
+
+
+def fit_chi2(c: Config, hits, cand, params, n_threads: int = 1) -> np.ndarray:
+    """chi2 of each frozen candidate (rows of 4 global hit indices, layers 0..3) at the
+    given alignment and field scale; NaN where a fit is invalid."""
+    h = np.ascontiguousarray(hits, np.int32)
+    q = np.ascontiguousarray(cand, np.int32).reshape(-1, 4)
+    _, pr = _dp(params)
+    out = np.empty(max(q.shape[0], 1))
+    lib().orc_fit_chi2(C.byref(c), h.ctypes.data_as(C.POINTER(C.c_int32)), h.size,
+                       q.ctypes.data_as(C.POINTER(C.c_int32)), q.shape[0], pr,
+                       out.ctypes.data_as(C.POINTER(C.c_double)), n_threads)
+    return out[:q.shape[0]]
+
+
+FD_STEPS = ([1e-4] * 3 + [1e-6] * 3) * 4 + [1e-6]  # central-difference steps: mm, rad, scale
+
+
+def fit_grad_fd(c: Config, hits, cand, params, n_threads: int = 1, steps=None):
+    """Sum of chi2 over the candidates valid at ``params`` and its gradient by central
+    differences in FP64 (the definition of the derivative, error O(h^2)): the
+    reference for the gradient kernel.  Returns (sum, grad[25], valid mask)."""
+    p0 = np.array(params, np.float64)
+    base = fit_chi2(c, hits, cand, p0, n_threads)
+    ok = np.isfinite(base)
+    sel = np.ascontiguousarray(np.asarray(cand, np.int32).reshape(-1, 4)[ok])
+    g = np.zeros(N_PARAMS)
+    for i, h in enumerate(steps or FD_STEPS):
+        pp, pm = p0.copy(), p0.copy()
+        pp[i] += h
+        pm[i] -= h
+        fp = fit_chi2(c, hits, sel, pp, n_threads)
+        fm = fit_chi2(c, hits, sel, pm, n_threads)
+        if not (np.isfinite(fp).all() and np.isfinite(fm).all()):
+            raise RuntimeError(f"a candidate's fit fails under the step of parameter {i}")
+        g[i] = (fp.sum() - fm.sum()) / (2.0 * h)
+    return float(base[ok].sum()), g, ok

@@ -80,11 +80,25 @@ def _target_points(rng, n, geo: Geometry):
     return rho * np.cos(ph), rho * np.sin(ph), z
 
 
-def _propagate(geo: Geometry, x, y, z, p, theta, psi, q, rng, ms: bool):
+def rotation(w) -> np.ndarray:
+    """R = Rz(wz) Ry(wy) Rx(wx): the rotation of a displaced layer (detector model)."""
+    cx, sx, cy, sy, cz, sz = (math.cos(w[0]), math.sin(w[0]), math.cos(w[1]), math.sin(w[1]),
+                              math.cos(w[2]), math.sin(w[2]))
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+def _propagate(geo: Geometry, x, y, z, p, theta, psi, q, rng, ms: bool, align=None):
     """Exact helix propagation (B along +z, positive charge turns clockwise) through
     the four cylinders in layer order, outward crossings only.  A track stops at the
     first layer it misses (curls back before reaching it, or leaves |z| <= H).
-    Returns a list over layers of (ok, x, y, z) arrays."""
+    With ``align`` (4 x 6: dx, dy, dz, wx, wy, wz per layer) layer L is the nominal
+    cylinder moved to R(w) x + d: the crossing is found by Newton steps from the
+    nominal one and the hit is reported in the layer's own (nominal) frame.
+    Returns a list over layers of (ok, x, y, z, xl, yl, zl) arrays: the global and
+    the layer-frame crossing points."""
     n = p.shape[0]
     alive = np.ones(n, bool)
     x = x.copy(); y = y.copy(); z = z.copy(); theta = theta.copy(); psi = psi.copy()
@@ -111,7 +125,26 @@ def _propagate(geo: Geometry, x, y, z, p, theta, psi, q, rng, ms: bool):
         nx = np.where(first1, p1x, p2x)
         ny = np.where(first1, p1y, p2y)
         nz = z + Rt * alpha * ct / np.where(st != 0.0, st, 1.0)
-        ok = reach & (np.abs(nz) <= geo.H[L])
+        cot = ct / np.where(st != 0.0, st, 1.0)
+        lx, ly, lz = nx, ny, nz
+        if align is not None:
+            Rm, dv = rotation(align[L][3:]), np.asarray(align[L][:3], float)
+            ang0 = np.arctan2(y - cy, x - cx)
+            for _ in range(4):  # Newton on |(R^T (h(alpha) - d))_xy|^2 = r^2
+                ang = ang0 - q * alpha
+                h = np.stack([cx + Rt * np.cos(ang), cy + Rt * np.sin(ang), z + Rt * alpha * cot], 1) - dv
+                dh = np.stack([Rt * q * np.sin(ang), -Rt * q * np.cos(ang), Rt * cot], 1)
+                loc, dloc = h @ Rm, dh @ Rm  # rows: R^T h
+                f = loc[:, 0] ** 2 + loc[:, 1] ** 2 - rL * rL
+                df = 2.0 * (loc[:, 0] * dloc[:, 0] + loc[:, 1] * dloc[:, 1])
+                alpha = alpha - np.where(reach & (df != 0.0), f / np.where(df != 0.0, df, 1.0), 0.0)
+            ang = ang0 - q * alpha
+            nx, ny, nz = cx + Rt * np.cos(ang), cy + Rt * np.sin(ang), z + Rt * alpha * cot
+            loc = (np.stack([nx, ny, nz], 1) - dv) @ Rm
+            lx, ly, lz = loc[:, 0], loc[:, 1], loc[:, 2]
+        ok = reach & (np.abs(lz) <= geo.H[L])
+        if align is not None:
+            ok &= alpha > 0.0  # Newton stays on the forward branch
         psi_n = psi - q * alpha
         if ms:
             sig = highland(1.0, geo.x0[L]) / p
@@ -126,7 +159,7 @@ def _propagate(geo: Geometry, x, y, z, p, theta, psi, q, rng, ms: bool):
             psi_n = np.arctan2(dy, dx)
         x, y, z, psi = nx, ny, nz, psi_n
         alive = ok
-        out.append((ok, nx, ny, nz))
+        out.append((ok, nx, ny, nz, lx, ly, lz))
     return out
 
 
@@ -186,7 +219,7 @@ def _digitise(geo: Geometry, L: int, x, y, z):
 # --------------------------------------------------------------------------- frames
 
 def _gen_chunk(geo, rng, f0, nf, n_tracks, signal_mask, noise_mean, ms, digitise, noise, p_range,
-               cos_range):
+               cos_range, align=None):
     # background tracks
     nt = int(n_tracks.sum())
     tf = np.repeat(np.arange(f0, f0 + nf), n_tracks)
@@ -214,14 +247,14 @@ def _gen_chunk(geo, rng, f0, nf, n_tracks, signal_mask, noise_mean, ms, digitise
         q = np.concatenate([q, np.tile([1.0, -1.0, 1.0], ns)])
         sig = np.concatenate([sig, np.ones(3 * ns, bool)])
     ntr = tf.size
-    layers = _propagate(geo, vx, vy, vz, np.maximum(p, 1e-6), theta, psi, q, rng, ms)
+    layers = _propagate(geo, vx, vy, vz, np.maximum(p, 1e-6), theta, psi, q, rng, ms, align)
     h_frame, h_addr, h_trk, h_pos, h_layer = [], [], [], [], []
     nh = np.zeros(ntr, np.int32)
-    for L, (ok, x, y, z) in enumerate(layers):
+    for L, (ok, x, y, z, xl, yl, zl) in enumerate(layers):
         idx = np.nonzero(ok)[0]
         nh[idx] += 1
         h_frame.append(tf[idx]); h_trk.append(idx); h_layer.append(np.full(idx.size, L, np.int8))
-        h_addr.append(_digitise(geo, L, x[idx], y[idx], z[idx]))
+        h_addr.append(_digitise(geo, L, xl[idx], yl[idx], zl[idx]))
         h_pos.append(np.stack([x[idx], y[idx], z[idx]], 1))
     if noise:
         for L in range(4):
@@ -246,16 +279,18 @@ def _gen_chunk(geo, rng, f0, nf, n_tracks, signal_mask, noise_mean, ms, digitise
 
 def _chunk_job(job):
     """One independently seeded chunk of frames (a process-pool task)."""
-    cfg, seed, c0, nf, counts, fsig, lam, ms, digitise, noise, p_range, cos_range = job
+    cfg, seed, c0, nf, counts, fsig, lam, ms, digitise, noise, p_range, cos_range, align, b_scale = job
     rng = np.random.default_rng([seed, 1 + c0 // CHUNK_FRAMES])
-    return _gen_chunk(Geometry(cfg), rng, c0, nf, counts, fsig, lam, ms, digitise, noise, p_range, cos_range)
+    geo = Geometry(cfg)
+    geo.B *= b_scale
+    return _gen_chunk(geo, rng, c0, nf, counts, fsig, lam, ms, digitise, noise, p_range, cos_range, align)
 
 
 def generate(n_frames: int, mean_tracks=10.0, noise_per_layer=0.5, signal_every: int | None = 10,
              seed: int = 1, ms: bool = True, digitise: bool = True, noise: bool = True,
              track_counts: np.ndarray | None = None, noise_scale: np.ndarray | None = None,
              p_range=(15.0, 53.0), cos_range=(-0.8, 0.8), cfg: dict | None = None,
-             workers: int | None = None) -> dict:
+             workers: int | None = None, align=None, b_scale: float = 1.0) -> dict:
     """Draw ``n_frames`` frames.
 
     mean_tracks      Poisson mean of background tracks per frame (ignored if track_counts given)
@@ -266,6 +301,10 @@ def generate(n_frames: int, mean_tracks=10.0, noise_per_layer=0.5, signal_every:
     noise_scale      per-frame multiplier of noise_per_layer
     workers          processes for chunks of 65,536 frames (spawned; the output does
                      not depend on it)
+    align            4 x 6 true displacement of the layers (dx, dy, dz [mm], wx, wy, wz
+                     [rad], layer L moved to R(w) x + d, R = Rz Ry Rx); hits are
+                     digitised in each layer's own frame
+    b_scale          true field / nominal field
     Returns dict with ``hits`` (int32), ``off`` (int64, F+1), per-hit truth ``hit_track``
     (global track id or -1), ``hit_layer``, ``hit_pos`` (float64 true crossing points of
     track hits, pixel centres of noise hits), per-track truth ``trk_*`` and
@@ -289,7 +328,7 @@ def generate(n_frames: int, mean_tracks=10.0, noise_per_layer=0.5, signal_every:
         nf = min(CHUNK_FRAMES, n_frames - c0)
         lam = noise_per_layer if noise_scale is None else noise_per_layer * np.asarray(noise_scale[c0:c0 + nf], float)
         jobs.append((cfg, seed, c0, nf, track_counts[c0:c0 + nf], fsig[c0:c0 + nf], lam, ms, digitise, noise,
-                     p_range, cos_range))
+                     p_range, cos_range, None if align is None else np.asarray(align, float), float(b_scale)))
     if workers is None:
         import sys
         main_file = getattr(sys.modules.get("__main__"), "__file__", None)
@@ -323,6 +362,14 @@ def generate(n_frames: int, mean_tracks=10.0, noise_per_layer=0.5, signal_every:
 
 # --------------------------------------------------------------------------- named workloads
 
+def c4_truth(seed: int = 4) -> dict:
+    """Injected misalignment of the c4 workload: per layer N(0, 50 um) in x, y, z and
+    N(0, 0.5 mrad) in the three rotations, field scale 1 + N(0, 1e-3)."""
+    rng = np.random.default_rng([seed, 0xa119])
+    align = np.concatenate([rng.normal(0.0, 0.050, (4, 3)), rng.normal(0.0, 0.5e-3, (4, 3))], 1)
+    return dict(align=align, b_scale=1.0 + rng.normal(0.0, 1e-3))
+
+
 def workload(name: str, n_frames: int | None = None, seed: int | None = None) -> dict:
     """The synthetic workloads: ``c1`` (parity: Poisson(10) tracks, 0.5 noise/layer,
     signal every 10th frame), ``c2`` (throughput: Poisson(20), 2 noise/layer, signal in
@@ -330,6 +377,13 @@ def workload(name: str, n_frames: int | None = None, seed: int | None = None) ->
     0.5 noise/layer, 1% of frames at 100x noise), ``c5`` (streaming: the c1 frame mix,
     signal every 10th frame, 1,000,000 frames, seed 5; the arrival process is the
     replay's)."""
+    if name == "c4":
+        # the c1 mix with the layers displaced and the field off nominal (seed 4)
+        s = seed if seed is not None else 4
+        truth = c4_truth(s)
+        out = generate(n_frames or 100_000, 10.0, 0.5, 10, s, align=truth["align"], b_scale=truth["b_scale"])
+        out.update(truth_align=truth["align"], truth_b_scale=truth["b_scale"])
+        return out
     if name == "c5":
         return generate(n_frames or 1_000_000, 10.0, 0.5, 10, seed if seed is not None else 5)
     if name == "c1":
