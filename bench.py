@@ -55,9 +55,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters (no autotuner)")
-    ap.add_argument("--arms", default="main,forms,e2e,c3,c5",
+    ap.add_argument("--arms", default="main,forms,e2e,c3,c4,c5",
                     help="comma list of measurements: main (staged, always), forms (fused and plain), e2e, c3, "
-                         "c5 (streaming latency)")
+                         "c4 (alignment gradient), c5 (streaming latency)")
     ap.add_argument("--c5-frames", type=int, default=1_000_000)
     return ap.parse_args()
 
@@ -211,6 +211,104 @@ def run_reference(args, rank, world):
                                        "sample": sample},
                       "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
           flush=True)
+
+
+ALIGN_SCALE = np.array(([0.05] * 3 + [5e-4] * 3) * 4 + [1.0])  # mm, rad, field scale: the c4 truth's widths
+
+
+def _euler_zyx(R):
+    """(wx, wy, wz) of R = Rz(wz) Ry(wy) Rx(wx)."""
+    return np.array([np.arctan2(R[2, 1], R[2, 2]), -np.arcsin(np.clip(R[2, 0], -1, 1)), np.arctan2(R[1, 0], R[0, 0])])
+
+
+def _relative_to_layer0(p, gen):
+    """Each layer's displacement relative to layer 0 (the common translation and
+    rotation of all layers leave every chi2 unchanged)."""
+    p = np.asarray(p, float)
+    R0, d0 = gen.rotation(p[3:6]), p[0:3]
+    out = np.zeros((4, 6))
+    for L in range(4):
+        RL, dL = gen.rotation(p[6 * L + 3:6 * L + 6]), p[6 * L:6 * L + 3]
+        out[L, :3] = R0.T @ (dL - d0)
+        out[L, 3:] = _euler_zyx(R0.T @ RL)
+    return out
+
+
+def align_arm(ctx, gen, m3e, n_frames: int, dev, steps: int = 200) -> dict:
+    """c4: frames from a displaced detector, the selection's kept tracks (at nominal
+    geometry, frozen), the gradient kernel's throughput, and 200 Adam steps on the
+    alignment of layers 1-3 (layer 0 fixed: common translation and z-rotation are
+    exact null modes; the field scale fixed: the chi2 sum is quadratic in it)."""
+    import torch
+    d = gen.workload("c4", n_frames=n_frames)
+    truth = np.r_[d["truth_align"].reshape(-1), d["truth_b_scale"]]
+    hits, off = torch.from_numpy(d["hits"]).to(dev), torch.from_numpy(d["off"]).to(dev)
+    rec = {k: v.cpu().numpy() for k, v in ctx.select_frames_debug(hits, off).items()}
+    cand = m3e.kept_candidates(rec, d["off"])
+    cq = torch.from_numpy(cand).to(dev)
+    nominal = torch.tensor(np.r_[np.zeros(24), 1.0], dtype=torch.float32, device=dev)
+
+    def time_calls(grad):
+        for _ in range(3):
+            ctx.fit_grad(hits, off, cq, nominal, grad=grad)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            ctx.fit_grad(hits, off, cq, nominal, grad=grad)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 20
+
+    ms_grad, ms_fwd = time_calls(True), time_calls(False)
+    scale = torch.tensor(ALIGN_SCALE, dtype=torch.float32, device=dev)
+    free = torch.zeros(25, device=dev)
+    free[6:24] = 1.0
+    x = torch.zeros(25, device=dev, requires_grad=True)
+    opt = torch.optim.Adam([x], lr=0.1)
+    hist = []
+    for _ in range(steps):
+        opt.zero_grad()
+        loss = m3e.fit_chi2_sum(x * scale * free + nominal, ctx, hits, off, cq)
+        loss.backward()
+        opt.step()
+        hist.append(loss.item())
+    est = (x * scale * free + nominal).detach().cpu().numpy().astype(np.float64)
+    s_end = float(ctx.fit_grad(hits, off, cq, torch.tensor(est, dtype=torch.float32, device=dev), grad=False)[0])
+    s_truth = float(ctx.fit_grad(hits, off, cq, torch.tensor(truth, dtype=torch.float32, device=dev), grad=False)[0])
+    # modes: Hessian of the chi2 sum in the 18 free parameters (units of the injected
+    # widths), by central differences of the gradient kernel
+    fi = np.arange(6, 24)
+    H = np.zeros((18, 18))
+    for a, i in enumerate(fi):
+        h = 0.02 * ALIGN_SCALE[i]
+        gp = ctx.fit_grad(hits, off, cq, torch.tensor(est + h * (np.arange(25) == i), dtype=torch.float32,
+                                                       device=dev))[1].cpu().numpy()
+        gm = ctx.fit_grad(hits, off, cq, torch.tensor(est - h * (np.arange(25) == i), dtype=torch.float32,
+                                                       device=dev))[1].cpu().numpy()
+        H[:, a] = (gp[fi] - gm[fi]) / (2 * h) * ALIGN_SCALE[fi] * ALIGN_SCALE[i]
+    ev, V = np.linalg.eigh(0.5 * (H + H.T))
+    rel_truth = _relative_to_layer0(truth, gen)[1:].reshape(-1) / ALIGN_SCALE[fi]
+    rel_est = _relative_to_layer0(est, gen)[1:].reshape(-1) / ALIGN_SCALE[fi]
+    res_m, tru_m = V.T @ (rel_est - rel_truth), V.T @ rel_truth
+    names = [f"L{1 + j // 6}{['dx', 'dy', 'dz', 'wx', 'wy', 'wz'][j % 6]}" for j in range(18)]
+    modes = [{"eigenvalue": float(ev[k]), "injected": float(tru_m[k]), "residual": float(res_m[k]),
+              "main_params": [names[j] for j in np.argsort(-np.abs(V[:, k]))[:3]]} for k in range(18)]
+    stiff = ev >= 1e-2 * ev.max()
+    trk = d["hit_track"][cand]
+    return {"workload": f"c4: {n_frames:,} frames of the c1 mix from a detector with layers displaced by "
+                        "N(0, 50 um) and N(0, 0.5 mrad) per axis and the field off by N(0, 1e-3), seed 4",
+            "candidates": int(cand.shape[0]),
+            "truth_matched_fraction": float(((trk[:, 0] >= 0) & (trk == trk[:, :1]).all(1)).mean()),
+            "fit_grad_ms": ms_grad, "fit_chi2_only_ms": ms_fwd,
+            "candidates_per_s_gradient": cand.shape[0] / (ms_grad / 1e3),
+            "steps": steps, "optimizer": "Adam lr 0.1 in units of the injected widths; layer 0 and field scale fixed",
+            "chi2_start": hist[0], "chi2_end": s_end, "chi2_at_truth": s_truth,
+            "stiff_modes": int(stiff.sum()),
+            "stiff_residual_over_injected": float(np.linalg.norm(res_m[stiff]) / np.linalg.norm(tru_m[stiff])),
+            "weak_residual_over_injected": float(np.linalg.norm(res_m[~stiff]) / max(np.linalg.norm(tru_m[~stiff]),
+                                                                                        1e-30)),
+            "modes": modes}
 
 
 C5_RATES = (15.625e6 / 12, 15.625e6 / 4, 15.625e6)
@@ -397,6 +495,10 @@ def main():
                            f"{f_mhz:.0f} MHz (median sampled under load)",
             "stages": stages,
             "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf}
+    # alignment gradient (c4)
+    c4 = None
+    if "c4" in arms and world == 1:
+        c4 = align_arm(ctx, gen, m3e, 100_000, dev)
     # streaming (c5): open-loop Poisson arrivals at the frame rates of 1e8 muons/s
     # (64 ns frames) divided by 12, 4 and 1, frame by frame through m3e_stream_submit
     c5 = None
@@ -415,6 +517,7 @@ def main():
            "reasons": dict(zip(m3e.REASONS, stats["reasons"][:7])),
            "tuning": tuning,
            "uneven_frames_c3": c3,
+           "alignment_c4": c4,
            "streaming_c5": c5,
            "roofline": roof, "e2e": e2e, "clocks": cl, "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

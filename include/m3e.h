@@ -249,6 +249,45 @@ int m3e_stage_times(m3e_ctx* ctx, float* ms, int n);
 int m3e_select_frames_noalloc(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
                               uint8_t* d_keep, uint8_t* d_reason, cudaStream_t stream);
 
+/* ------------------------------------------------------------------ fit gradient
+ *
+ * Gradient of the summed track chi2 of frozen candidates with respect to the
+ * rigid alignment of the four layers and the field scale (an extension for
+ * detector alignment; the paper's track fit, Sec. "Track Reconstruction", is the
+ * forward model, the paper itself fits no alignment).
+ *   - d_cand: n_cand rows of 4 int32, the global indices into d_hits of a
+ *     layer-0, -1, -2 and -3 hit (16-byte aligned), e.g. the quadruplets of
+ *     tracks the selection kept.  The selection is discrete: the rows stay
+ *     fixed while the parameters move.
+ *   - d_params: 25 floats.  Layer L: params[6L .. 6L+5] = dx, dy, dz [mm],
+ *     wx, wy, wz [rad]; the hit measured at nominal position x on layer L is
+ *     placed at R(w) x + d, R = Rz(wz) Ry(wy) Rx(wx) (rotations about the global
+ *     axes through the origin).  params[24] scales the field (1 = nominal).
+ *   - chi2 of a candidate: the track chi2 of the selection (two triplet fits,
+ *     global chi2 at the inverse-variance mean curvature) at the moved hits;
+ *     candidates whose fit fails, or whose hits are invalid, out of range
+ *     (index >= d_frame_off[n_frames]) or on the wrong layer, are left out.
+ *   - *d_chi2_sum (device float) = sum of chi2 over the valid candidates;
+ *     d_grad (device float[25], or NULL for the sum alone) = its gradient.
+ * The gradient is reverse mode, recomputing each candidate's fit (nothing per
+ * candidate is stored).  A common translation of all layers and a common
+ * rotation about z leave every chi2 unchanged (the gradient has no component
+ * along them), and chi2 is quadratic in the field scale.  Sums are accumulated in
+ * FP64 per block and added in a fixed order: repeated calls give equal results.
+ * Asynchronous on `stream`. */
+int m3e_fit_grad(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                 const int32_t* d_cand, int64_t n_cand, const float* d_params, float* d_chi2_sum, float* d_grad,
+                 cudaStream_t stream);
+
+/* chi2 of each candidate (NaN for those left out) into d_chi2_each[n_cand]. */
+int m3e_fit_chi2(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                 const int32_t* d_cand, int64_t n_cand, const float* d_params, float* d_chi2_each,
+                 cudaStream_t stream);
+
+/* Number of valid candidates of the last m3e_fit_grad / m3e_fit_chi2 call
+ * (synchronises `stream`). */
+int m3e_fit_valid_count(m3e_ctx* ctx, cudaStream_t stream, int64_t* out);
+
 /* ------------------------------------------------------------------ streaming
  *
  * Frame-by-frame submission with continuous batching: the filter-farm setting

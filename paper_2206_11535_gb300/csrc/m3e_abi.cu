@@ -112,6 +112,11 @@ struct m3e_ctx {
   cudaEvent_t pe[10] = {};
   // streaming
   StreamEngine* stream = nullptr;
+  // fit gradient: per-block partial sums and the valid-candidate counter
+  double* fit_partial = nullptr;
+  int fit_partial_blocks = 0;
+  unsigned long long* fit_nvalid = nullptr;
+  unsigned long long* h_fit_nvalid = nullptr;
 };
 
 namespace {
@@ -458,6 +463,9 @@ int m3e_destroy(m3e_ctx* x) {
   if (x->stream) stream_destroy(x->stream);
   x->stream = nullptr;
   cudaDeviceSynchronize();
+  cudaFree(x->fit_partial);
+  cudaFree(x->fit_nvalid);
+  if (x->h_fit_nvalid) cudaFreeHost(x->h_fit_nvalid);
   cudaFree(x->col_lut);
   cudaFree(x->row_lut);
   cudaFree(x->err);
@@ -989,4 +997,61 @@ int m3e_stream_replay(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_frame_
   }
   return stream_replay(x->stream, h_hits, h_frame_off, n_frames, rate_hz, seed, out_keep, out_reason,
                        out_lat_submit_ns, out_lat_arrival_ns, out);
+}
+
+// ------------------------------------------------------------------ fit gradient
+
+namespace {
+
+int fit_call(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n_frames, const int32_t* d_cand,
+             int64_t n_cand, const float* d_params, float* chi2_each, float* chi2_sum, float* grad, cudaStream_t s) {
+  if (!x) return fail(M3E_EINVAL, "ctx is NULL");
+  if (n_frames < 0 || n_cand < 0) return fail(M3E_EINVAL, "n_frames and n_cand must be >= 0");
+  if (!d_off || !d_params || (n_cand > 0 && (!d_cand || !d_hits)))
+    return fail(M3E_EINVAL, "frame_off, params, cand and hits must not be NULL");
+  if (((uintptr_t)d_cand & 15) != 0) return fail(M3E_EINVAL, "cand must be 16-byte aligned (rows of 4 int32)");
+  DeviceGuard guard(x->device);
+  const int nb = fit_grad_blocks(x->sms, n_cand);
+  if (nb > x->fit_partial_blocks) {
+    cudaFree(x->fit_partial);
+    x->fit_partial = nullptr;
+    x->fit_partial_blocks = 0;
+    CUDA_TRY(cudaMalloc(&x->fit_partial, sizeof(double) * fit_grad_partial_size() * (size_t)nb));
+    x->fit_partial_blocks = nb;
+  }
+  if (!x->fit_nvalid) CUDA_TRY(cudaMalloc(&x->fit_nvalid, sizeof(unsigned long long)));
+  CUDA_TRY(cudaMemsetAsync(x->fit_nvalid, 0, sizeof(unsigned long long), s));
+  CUDA_TRY(launch_fit_grad(x->dc, d_hits, d_off, n_frames, d_cand, n_cand, d_params, x->col_lut, x->row_lut,
+                           x->fit_partial, nb, x->fit_nvalid, chi2_each, chi2_sum, grad, s));
+  return M3E_OK;
+}
+
+}  // namespace
+
+int m3e_fit_grad(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                 const int32_t* d_cand, int64_t n_cand, const float* d_params, float* d_chi2_sum, float* d_grad,
+                 cudaStream_t stream) {
+  if (!d_chi2_sum) return fail(M3E_EINVAL, "chi2_sum must not be NULL");
+  return fit_call(x, d_hits, d_frame_off, n_frames, d_cand, n_cand, d_params, nullptr, d_chi2_sum, d_grad, stream);
+}
+
+int m3e_fit_chi2(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                 const int32_t* d_cand, int64_t n_cand, const float* d_params, float* d_chi2_each,
+                 cudaStream_t stream) {
+  if (!d_chi2_each && n_cand > 0) return fail(M3E_EINVAL, "chi2_each must not be NULL");
+  return fit_call(x, d_hits, d_frame_off, n_frames, d_cand, n_cand, d_params, d_chi2_each, nullptr, nullptr,
+                  stream);
+}
+
+int m3e_fit_valid_count(m3e_ctx* x, cudaStream_t stream, int64_t* out) {
+  if (!x || !out) return fail(M3E_EINVAL, "ctx or out is NULL");
+  *out = 0;
+  if (!x->fit_nvalid) return M3E_OK;
+  DeviceGuard guard(x->device);
+  if (!x->h_fit_nvalid) CUDA_TRY(cudaMallocHost(&x->h_fit_nvalid, sizeof(unsigned long long)));
+  CUDA_TRY(cudaMemcpyAsync(x->h_fit_nvalid, x->fit_nvalid, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  *out = (int64_t)*x->h_fit_nvalid;
+  return M3E_OK;
 }

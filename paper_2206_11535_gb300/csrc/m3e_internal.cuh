@@ -104,6 +104,14 @@ int stage_blocks_per_sm(int stage);
 size_t fused_smem_bytes();
 size_t cta_smem_bytes();
 
+// Gradient of the fit chi2 (m3e_grad.cu).
+int fit_grad_blocks(int sms, int64_t n_cand);
+int fit_grad_partial_size();
+cudaError_t launch_fit_grad(const DevCfg& c, const int32_t* hits, const int64_t* off, int64_t n_frames,
+                            const int32_t* cand, int64_t n_cand, const float* params, const float4* col_lut,
+                            const float* row_lut, double* partial, int nblocks, unsigned long long* n_valid,
+                            float* chi2_each, float* chi2_sum, float* grad, cudaStream_t s);
+
 // Records the calling thread's error message (m3e_last_error_string) and returns code.
 int m3e_set_error(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 

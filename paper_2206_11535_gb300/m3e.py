@@ -108,6 +108,9 @@ def _load(path: str = LIB_PATH):
     lib.m3e_last_launch_count.argtypes = [vp]
     lib.m3e_last_error_string.restype = C.c_char_p
     lib.m3e_set_profiling.argtypes = [vp, C.c_int]
+    lib.m3e_fit_grad.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
+    lib.m3e_fit_chi2.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp]
+    lib.m3e_fit_valid_count.argtypes = [vp, vp, C.POINTER(C.c_int64)]
     lib.m3e_stream_open.argtypes = [vp, C.POINTER(StreamParams)]
     lib.m3e_stream_submit.argtypes = [vp, vp, C.c_int32, C.c_uint64, vp]
     lib.m3e_stream_submit_many.argtypes = [vp, vp, vp, i64, vp, vp, C.POINTER(C.c_int64)]
@@ -320,6 +323,34 @@ class Context:
         return a.value, b.value
 
 
+    # ---------------------------------------------------------------- fit gradient
+
+    def fit_grad(self, hits, off, cand, params, grad: bool = True, stream=None):
+        """``m3e_fit_grad``: (chi2 sum, gradient[25] or None) as float32 device tensors.
+        cand: int32 device tensor (n, 4) of global hit indices; params: float32 (25,)."""
+        import torch
+        dev = hits.device
+        s = torch.empty(1, dtype=torch.float32, device=dev)
+        g = torch.empty(25, dtype=torch.float32, device=dev) if grad else None
+        c = cand.contiguous()
+        _check(lib.m3e_fit_grad(self._h, _ptr(hits), _ptr(off), off.numel() - 1, _ptr(c), c.shape[0],
+                                _ptr(params.contiguous()), _ptr(s), _ptr(g), _stream(stream)))
+        return s, g
+
+    def fit_chi2(self, hits, off, cand, params, stream=None):
+        """``m3e_fit_chi2``: chi2 of each candidate (NaN where left out)."""
+        import torch
+        c = cand.contiguous()
+        out = torch.empty(c.shape[0], dtype=torch.float32, device=hits.device)
+        _check(lib.m3e_fit_chi2(self._h, _ptr(hits), _ptr(off), off.numel() - 1, _ptr(c), c.shape[0],
+                                _ptr(params.contiguous()), _ptr(out), _stream(stream)))
+        return out
+
+    def fit_valid_count(self, stream=None) -> int:
+        n = C.c_int64()
+        _check(lib.m3e_fit_valid_count(self._h, _stream(stream), C.byref(n)))
+        return n.value
+
     # ---------------------------------------------------------------- streaming
 
     def stream_open(self, **params):
@@ -422,3 +453,54 @@ def stats_dict(t) -> dict:
 def new_stats(device="cuda"):
     import torch
     return torch.zeros(N_STATS, dtype=torch.int64, device=device)
+
+
+def kept_candidates(rec: dict, off, min_status: int = 5):
+    """Quadruplets (global hit indices, int32 (n, 4)) of the tracks a debug selection
+    record holds with track status >= min_status (5: kept by the chi2 cut)."""
+    import numpy as _np
+    n_trip = _np.asarray(rec["n_trip"])
+    trip = _np.asarray(rec["trip"])
+    st = _np.asarray(rec["trk_status"])
+    cap = trip.shape[1]
+    f_idx, t_idx = _np.nonzero((_np.arange(cap)[None, :] < _np.minimum(n_trip, cap)[:, None]) & (st >= min_status))
+    q = trip[f_idx, t_idx, :4].astype(_np.int64) + _np.asarray(off)[f_idx][:, None]
+    return _np.ascontiguousarray(q.astype(_np.int32))
+
+
+def _fit_chi2_function():
+    import torch
+
+    class FitChi2(torch.autograd.Function):
+        """Sum of the track chi2 of frozen candidates as a function of the 25 alignment
+        and field-scale parameters.  Forward runs m3e_fit_grad without the gradient;
+        backward runs it again with the gradient (the fit is recomputed, nothing per
+        candidate is kept between the two)."""
+
+        @staticmethod
+        def forward(fctx, params, m3e_ctx, hits, off, cand):
+            p = params.detach().to(torch.float32).contiguous()
+            s, _ = m3e_ctx.fit_grad(hits, off, cand, p, grad=False)
+            fctx.save_for_backward(p)
+            fctx.m3e = (m3e_ctx, hits, off, cand)
+            return s[0].to(params.dtype)
+
+        @staticmethod
+        def backward(fctx, g_out):
+            (p,) = fctx.saved_tensors
+            m3e_ctx, hits, off, cand = fctx.m3e
+            _, g = m3e_ctx.fit_grad(hits, off, cand, p, grad=True)
+            return (g_out * g).to(p.dtype), None, None, None, None
+
+    return FitChi2
+
+
+_FIT = None
+
+
+def fit_chi2_sum(params, ctx: "Context", hits, off, cand):
+    """Differentiable sum of the track chi2 (torch.autograd.Function over m3e_fit_grad)."""
+    global _FIT
+    if _FIT is None:
+        _FIT = _fit_chi2_function()
+    return _FIT.apply(params, ctx, hits, off, cand)
