@@ -513,6 +513,7 @@ def main():
                       "parallelism": f"{world} independent GPU shard(s), no collective on the data path"},
            "hits_per_s": world * nh * args.steps / (ms / 1e3),
            **(forms or {}),
+           "work_per_frame": {k: stats[k] / nf for k in m3e.STATS_FIELDS if k not in ("frames",)},
            "kept_fraction": float(keep.float().mean().item()),
            "reasons": dict(zip(m3e.REASONS, stats["reasons"][:7])),
            "tuning": tuning,
