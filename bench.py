@@ -55,9 +55,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters (no autotuner)")
-    ap.add_argument("--arms", default="main,forms,e2e,c3,c4,c5",
+    ap.add_argument("--arms", default="main,forms,e2e,c3,c4,c5,rates",
                     help="comma list of measurements: main (staged, always), forms (fused and plain), e2e, c3, "
-                         "c4 (alignment gradient), c5 (streaming latency)")
+                         "c4 (alignment gradient), c5 (streaming latency), rates (muon-rate sweep)")
     ap.add_argument("--c5-frames", type=int, default=1_000_000)
     return ap.parse_args()
 
@@ -311,6 +311,41 @@ def align_arm(ctx, gen, m3e, n_frames: int, dev, steps: int = 200) -> dict:
             "modes": modes}
 
 
+MU_RATES = (1e8, 2e8, 5e8, 1e9)
+
+
+def rate_arm(ctx, gen, m3e, n_frames: int, dev, steps: int = 5) -> dict:
+    """Muon-rate sweep: 64 ns frames hold Poisson(6.4 x rate / 1e8) decay tracks
+    (6.4 at the paper's 1e8 muons/s), 0.5 noise hits per layer, a signal decay in
+    every 1000th frame.  Staged-form frames/s and the kept fraction by reason."""
+    import torch
+    out = []
+    for k, rate in enumerate(MU_RATES):
+        d = gen.generate(n_frames, 6.4 * rate / 1e8, 0.5, 1000, seed=60 + k)
+        hits, off = torch.from_numpy(d["hits"]).to(dev), torch.from_numpy(d["off"]).to(dev)
+        nf = n_frames
+        keep = torch.empty(nf, dtype=torch.uint8, device=dev)
+        reason = torch.empty(nf, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            ctx.select_frames(hits, off, keep, reason)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            ctx.select_frames(hits, off, keep, reason)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        r = reason.cpu().numpy()
+        out.append({"muons_per_s": rate, "mean_tracks_per_frame": 6.4 * rate / 1e8,
+                    "hits_per_frame": float(d["off"][-1]) / nf, "frames_per_s": nf / (ms / 1e3),
+                    "ms_per_batch": ms, "kept_fraction": float((r != 0).mean()),
+                    "kept_by_reason": {m3e.REASONS[i]: float((r == i).mean()) for i in range(1, 7)}})
+        del hits, off, keep, reason
+    return {"workload": f"{n_frames:,} frames per rate, tracks Poisson(6.4 x rate / 1e8), 0.5 noise/layer, "
+                        "signal every 1000th frame, seeds 60-63", "rates": out}
+
+
 C5_RATES = (15.625e6 / 12, 15.625e6 / 4, 15.625e6)
 
 
@@ -495,6 +530,10 @@ def main():
                            f"{f_mhz:.0f} MHz (median sampled under load)",
             "stages": stages,
             "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf}
+    # muon-rate sweep
+    rates = None
+    if "rates" in arms and world == 1:
+        rates = rate_arm(ctx, gen, m3e, 200_000, dev)
     # alignment gradient (c4)
     c4 = None
     if "c4" in arms and world == 1:
@@ -518,6 +557,7 @@ def main():
            "reasons": dict(zip(m3e.REASONS, stats["reasons"][:7])),
            "tuning": tuning,
            "uneven_frames_c3": c3,
+           "rate_sweep": rates,
            "alignment_c4": c4,
            "streaming_c5": c5,
            "roofline": roof, "e2e": e2e, "clocks": cl, "gpu_launches": launches}

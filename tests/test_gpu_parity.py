@@ -273,3 +273,16 @@ def test_graph_and_autotune_keep_decisions(m3e, cfg):
                 assert (reason.cpu().numpy() == ref).all()
             g.close()
         ctx.check()
+
+
+def test_high_rate_sample(ctx, ocfg):
+    """Frames at 1e9 muons/s (Poisson(64) tracks): dense frames, CTA tiers and
+    triplet overflows, candidate by candidate."""
+    d = gen.generate(120, 64.0, 0.5, 1000, seed=63)
+    hits, off = _dev(d)
+    rec = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024, form=FORMS["staged"]))
+    s = _check_results(P.compare_batch(ocfg, d["hits"], d["off"], rec), max_boundary_frac=0.05)
+    print("1e9 muons/s sample parity", s)
+    for form in ("fused", "plain"):
+        rf = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024, form=FORMS[form]))
+        assert (rf["reason"] == rec["reason"]).all()
