@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cfloat>
+#include <type_traits>
 
 #include "m3e_internal.cuh"
 
@@ -49,11 +50,17 @@ struct TrkSoA {
   int tid[CK];                      // index of the triplet it came from
 };
 
-template <int CH, int CT, int CK, int CC, int CH32 = (CH <= W_HITS ? CH : 1)>
+// PHI / IDX: whether the stage keeps each hit's phi (the layer-3 search of the
+// fused track stage reads it) and its input index (candidate record only); a
+// stage without them holds more frames in flight per SM.  Triplets of a stage of
+// at most 256 hits are kept as 8-bit indices.
+template <int CH, int CT, int CK, int CC, bool PHI = true, bool IDX = true, int CH32 = (CH <= W_HITS ? CH : 1)>
 struct FrameSm {
-  float x[CH], y[CH], z[CH], phi[CH];
+  static constexpr bool kPhi = PHI, kIdx = IDX;
+  using TripT = typename std::conditional<(CH <= 256), uchar4, ushort4>::type;
+  float x[CH], y[CH], z[CH], phi[PHI ? CH : 1];
   uint32_t addr[CH];
-  uint16_t inidx[CH];
+  uint16_t inidx[IDX ? CH : 1];
   uint8_t bin[CH];
   uint16_t bstart[NBK + 1];
   int bcur[NBK];
@@ -65,7 +72,7 @@ struct FrameSm {
   int cst[CH32 + 1];
   TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
-    ushort4 trip[CT];           // selected triplets (sorted-hit indices)
+    TripT trip[CT];             // selected triplets (sorted-hit indices)
     uint32_t combo[CC];         // e+ e+ e- combinations (track indices), after the fits
   } u;
   int ntrip, npos, nneg, ncombo, flag, bad;
@@ -77,6 +84,16 @@ using SmWarp = FrameSm<W_HITS, W_TRIP, W_TRK, W_COMBO>;
 using SmCta = FrameSm<C_HITS, C_TRIP, C_TRK, C_COMBO>;
 
 // ------------------------------------------------------------------ small helpers
+
+template <class T>
+__device__ __forceinline__ T make_trip(int i0, int i1, int i2) {  // a triplet of sorted-hit indices
+  T t;
+  t.x = (decltype(t.x))i0;
+  t.y = (decltype(t.y))i1;
+  t.z = (decltype(t.z))i2;
+  t.w = 0;
+  return t;
+}
 
 struct Dec {
   int L, g, row, b;
@@ -705,10 +722,10 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     const float4 cl = __ldg(P.col_lut + C.col_off[d.L] + d.g);
     sm.x[pos] = cl.x;
     sm.y[pos] = cl.y;
-    sm.phi[pos] = cl.z;
+    if constexpr (S::kPhi) sm.phi[pos] = cl.z;
     sm.z[pos] = __ldg(P.row_lut + C.row_off[d.L] + d.row);
     sm.addr[pos] = a;
-    sm.inidx[pos] = (uint16_t)i;
+    if constexpr (S::kIdx) sm.inidx[pos] = (uint16_t)i;
     sm.bin[pos] = (uint8_t)d.b;
   }
   g.sync();
@@ -831,7 +848,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           }
           const unsigned m = __ballot_sync(FULL, pass);
           const int kk = nt + __popc(m & ((1u << lane) - 1u));
-          if (pass && kk < CT) sm.u.trip[kk] = make_ushort4((uint16_t)i0, (uint16_t)i1, (uint16_t)i2, 0);
+          if (pass && kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
           nt += __popc(m);
           if (nt > C.max_trip) break;  // the frame overflows: its decision is known
         }
@@ -873,7 +890,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
                 const float Qq = cr * cr;
                 if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
                 const int k = atomicAdd(&sm.ntrip, 1);
-                if (k < CT) sm.u.trip[k] = make_ushort4((uint16_t)i0, (uint16_t)i1, (uint16_t)i2, 0);
+                if (k < CT) sm.u.trip[k] = make_trip<typename S::TripT>(i0, i1, i2);
               }
             }
           }
@@ -904,7 +921,7 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
   const SmHits<S> view{sm};
   // ---- D: track reconstruction (Algorithm 3), one thread per triplet
   for (int t = g.rank(); t < ntrip; t += G::N) {
-    const ushort4 tr = sm.u.trip[t];
+    const auto tr = sm.u.trip[t];
     float tk[14];
     const TrackOut o = build_track(view, C, tr.x, tr.y, tr.z, tk);
     if (o.status == 5) {

@@ -18,7 +18,8 @@ namespace {
 
 constexpr int NL3 = NB + 1;                        // layer-3 bin starts per frame
 constexpr int S1_TRIP = 256;                       // stage-1 warp-tier triplet capacity
-using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1>;
+using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1, false, false>;  // phi re-read at emit, no input indices
+using SmFrontD = FrameSm<W_HITS, S1_TRIP, 1, 1>;                // candidate record: with input indices
 constexpr int M_HITS = 1024;                       // stage-1 middle tier (CTA per frame)
 using SmFrontMid = FrameSm<M_HITS, C_TRIP, 1, 1>;
 using SmFrontCta = FrameSm<C_HITS, C_TRIP, 1, 1>;
@@ -43,8 +44,8 @@ __device__ __forceinline__ int warp_count_add(int* ctr, bool pred) {  // ordered
 // Sorted hits and triplets go to global memory at places taken from the hit and
 // triplet allocators; a frame that does not fit is deferred (returns false).
 template <class G, class Sm, bool DEBUG>
-__device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const KParams& P, const SParams& S, int f, int n,
-                                           int ntrip, long long* bcast) {
+__device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, const KParams& P, const SParams& S,
+                                           int f, int n, int ntrip, long long* bcast) {
   if (g.leader()) {
     bcast[0] = (long long)atomicAdd(&S.counters[3], (unsigned long long)n);
     bcast[1] = (long long)atomicAdd(&S.counters[0], (unsigned long long)ntrip);
@@ -61,13 +62,21 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const KParams& P,
     S.hx[hb + i] = sm.x[i];
     S.hy[hb + i] = sm.y[i];
     S.hz[hb + i] = sm.z[i];
-    S.hphi[hb + i] = sm.phi[i];
+    if constexpr (Sm::kPhi) {
+      S.hphi[hb + i] = sm.phi[i];
+    } else {
+      const Dec d = decode(C, sm.addr[i]);
+      S.hphi[hb + i] = __ldg(P.col_lut + C.col_off[d.L] + d.g).z;
+    }
     S.haddr[hb + i] = sm.addr[i];
-    if (DEBUG) S.hidx[hb + i] = sm.inidx[i];
+    if constexpr (DEBUG) {
+      static_assert(Sm::kIdx, "the candidate record needs the input indices");
+      S.hidx[hb + i] = sm.inidx[i];
+    }
   }
   for (int b = g.rank(); b < NL3; b += G::N) S.l3[(int64_t)f * NL3 + b] = sm.bstart[3 * NB + b];
   for (int t = g.rank(); t < ntrip; t += G::N) {
-    const ushort4 q = sm.u.trip[t];
+    const auto q = sm.u.trip[t];
     S.trip[tb + t] = make_int4(f, q.x, q.y, q.z);
   }
   if (g.leader()) {
@@ -82,13 +91,13 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const KParams& P,
 
 // After frame_front: decide, emit, or defer one frame (stage-1 tiers).
 template <class G, class Sm, bool DEBUG>
-__device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const KParams& P, const SParams& S, int f, int r,
-                                              long long* bcast) {
+__device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const DevCfg& C, const KParams& P, const SParams& S,
+                                              int f, int r, long long* bcast) {
   const int ntrip = sm.ntrip;
   if (r == PENDING && ntrip == 0) r = M3E_DROP;  // no triplet: no track, no vertex
   if (r == PENDING) {
     const int n = (int)(P.off[f + 1] - P.off[f]);
-    if (emit_frame<G, Sm, DEBUG>(g, sm, P, S, f, n, ntrip, bcast)) {
+    if (emit_frame<G, Sm, DEBUG>(g, sm, C, P, S, f, n, ntrip, bcast)) {
       if (g.leader() && P.stats)
         for (int k = 0; k < ST_REASON0; ++k) sm.acc[k] += sm.facc[k];
     } else {
@@ -114,7 +123,8 @@ template <bool DEBUG>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     k_stage1(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmFront& sm = reinterpret_cast<SmFront*>(smem_raw)[threadIdx.x >> 5];
+  using Sm = typename std::conditional<DEBUG, SmFrontD, SmFront>::type;
+  Sm& sm = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
   __shared__ long long bcast[WARPS_PER_CTA][2];
   const WarpGroup g;
   clear_stats(g, sm);
@@ -126,8 +136,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     if (f0 >= nf) break;
     const int f1 = min(f0 + P.grab, nf);
     for (int f = f0; f < f1; ++f) {
-      const int r = frame_front<WarpGroup, SmFront, W_HITS, S1_TRIP, true, DEBUG>(g, sm, C, P, f);
-      stage1_finish<WarpGroup, SmFront, DEBUG>(g, sm, P, S, f, r, bcast[threadIdx.x >> 5]);
+      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG>(g, sm, C, P, f);
+      stage1_finish<WarpGroup, Sm, DEBUG>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
     }
   }
   flush_stats(g, sm, P.stats);
@@ -149,7 +159,7 @@ __global__ void __launch_bounds__(CTA_THREADS)
     int r;
     if (CH < C_HITS && P.off[f + 1] - P.off[f] > CH) r = DEFERRED;  // for the next tier
     else r = frame_front<CtaGroup<CTA_THREADS>, Sm, CH, C_TRIP, false, DEBUG>(g, sm, C, P, f);
-    stage1_finish<CtaGroup<CTA_THREADS>, Sm, DEBUG>(g, sm, P, S, f, r, bcast);
+    stage1_finish<CtaGroup<CTA_THREADS>, Sm, DEBUG>(g, sm, C, P, S, f, r, bcast);
   }
   flush_stats(g, sm, P.stats);
 }
@@ -454,7 +464,7 @@ cudaError_t set_smem(K k, size_t bytes) {
 
 }  // namespace
 
-size_t stage1_smem_bytes() { return sizeof(SmFront) * WARPS_PER_CTA; }
+size_t stage1_smem_bytes(bool debug = false) { return (debug ? sizeof(SmFrontD) : sizeof(SmFront)) * WARPS_PER_CTA; }
 size_t stage1c_smem_bytes() { return sizeof(SmFrontCta); }
 size_t stage1m_smem_bytes() { return sizeof(SmFrontMid); }
 
@@ -489,7 +499,7 @@ int stage_blocks_per_sm(int stage) {
 // null): before stage 1 and after each kernel.
 cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
                           cudaStream_t st, cudaEvent_t* ev) {
-  const size_t sm1 = stage1_smem_bytes(), smc = stage1c_smem_bytes(), smm = stage1m_smem_bytes();
+  const size_t sm1 = stage1_smem_bytes(debug), smc = stage1c_smem_bytes(), smm = stage1m_smem_bytes();
   cudaError_t e = debug ? set_smem(k_stage1<true>, sm1) : set_smem(k_stage1<false>, sm1);
   if (e == cudaSuccess)
     e = debug ? set_smem(k_stage1c<SmFrontCta, C_HITS, true>, smc) : set_smem(k_stage1c<SmFrontCta, C_HITS, false>, smc);
