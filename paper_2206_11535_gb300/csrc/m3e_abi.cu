@@ -160,6 +160,7 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
     d.ntot[L] = c.n_ladders[L] * c.n_cols[L];
     const double x = c.x_over_X0[L];
     d.hl[L] = (float)(13.6 * std::sqrt(x) * (1.0 + 0.038 * std::log(x)));
+    d.ihl[L] = (float)(1.0 / (13.6 * std::sqrt(x) * (1.0 + 0.038 * std::log(x))));
   }
   int co = 0, ro = 0;
   for (int L = 0; L < 4; ++L) {

@@ -152,25 +152,27 @@ struct SegF {
 // angle theta_C and the derivatives dPhi/dR, dtheta/dR at the circle solution.
 // sin(Phi/2) = d / 2R_t on either arc (the long arc turns by 2 pi minus the short
 // one, which leaves the sine of the half angle and flips its cosine).
-__device__ __forceinline__ SegF segment(float d, float z, float Rct, bool obtuse) {
+// inv2R = 1 / (2 R_t).  The divisions share the reciprocals of Phi and of
+// sin(Phi/2): dPhi/dR = -R_C / (d^2 cos(Phi/2) / (8 sin^3(Phi/2)) + zp^2 / Phi).
+__device__ __forceinline__ SegF segment(float d, float z, float Rct, float inv2R, bool obtuse) {
   SegF s;
-  const float sh = fminf(1.f, d / (2.f * Rct));
+  const float sh = fminf(1.f, d * inv2R);
   float ph = 2.f * asinf(sh);
   float ch = sqrtf(fmaxf((1.f - sh) * (1.f + sh), 0.f));
   if (obtuse) {
     ph = TWO_PI_F - ph;
     ch = -ch;
   }
-  const float zp = z / ph;
+  const float iph = 1.f / ph, ish = 1.f / sh;
+  const float zp = z * iph;
   s.RC = sqrtf(Rct * Rct + zp * zp);
   s.th = atan2f(Rct * ph, z);
-  const float sh2 = sh * sh;
-  const float dRdphi = -(d * d * ch / (8.f * sh2 * sh) + zp * zp / ph) / s.RC;
-  s.dphi = 1.f / dRdphi;
-  const float g = ph / (2.f * sh);
-  const float gp = sin_minus_xcos(0.5f * ph, sh, ch) / (2.f * sh2);
+  const float ish2 = ish * ish;
+  s.dphi = -s.RC / (0.125f * d * d * ch * ish2 * ish + zp * zp * iph);
+  const float g = 0.5f * ph * ish;
+  const float gp = 0.5f * sin_minus_xcos(0.5f * ph, sh, ch) * ish2;
   const float dg = d * g;
-  s.dth = z * d * gp / (z * z + dg * dg) * s.dphi;
+  s.dth = z * d * gp * s.dphi / (z * z + dg * dg);
   s.phi = ph;
   s.zp = zp;
   return s;
@@ -204,16 +206,18 @@ __device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx
   const float wx = cx - ax, wy = cy - ay;
   const float d01 = sqrtf(u2), d12 = sqrtf(v2), d20 = sqrtf(wx * wx + wy * wy);
   if (!(cross != 0.f)) return f;
-  const float rtc = d01 * d12 * d20 / (2.f * cross);
+  const float i2c = 0.5f / cross;
+  const float rtc = d01 * d12 * d20 * i2c;
   if (!isfinite(rtc) || rtc == 0.f) return f;
   f.Rct = fabsf(rtc);
   f.eps = rtc > 0.f ? 1.f : -1.f;
-  f.ccx = bx + (vy * u2 - uy * v2) / (2.f * cross);
-  f.ccy = by + (ux * v2 - vx * u2) / (2.f * cross);
+  f.ccx = bx + (vy * u2 - uy * v2) * i2c;
+  f.ccy = by + (ux * v2 - vx * u2) * i2c;
+  const float inv2R = 0.5f / f.Rct;
   const bool ob0 = ((ax - cx) * (bx - cx) + (ay - cy) * (by - cy)) < 0.f;
   const bool ob1 = ((bx - ax) * (cx - ax) + (by - ay) * (cy - ay)) < 0.f;
-  const SegF s0 = segment(d01, bz - az, f.Rct, ob0);
-  const SegF s1 = segment(d12, cz - bz, f.Rct, ob1);
+  const SegF s0 = segment(d01, bz - az, f.Rct, inv2R, ob0);
+  const SegF s1 = segment(d12, cz - bz, f.Rct, inv2R, ob1);
   const float dR = s0.RC - s1.RC;
   f.Rref = s0.RC;
   f.alpha = 0.5f * (s0.dphi + s1.dphi);
@@ -226,9 +230,9 @@ __device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx
   const float u = -(f.alpha * f.a0p * f.s2 + f.beta * f.b0p) / den;
   const float Rs = f.Rref + u;
   if (!(Rs > 0.f) || !isfinite(Rs)) return f;
-  const float sms = hl / (kB * Rs);
-  f.kappa = f.eps / Rs;
-  f.skappa = sms / sqrtf(den) / (Rs * Rs);
+  const float iRs = 1.f / Rs;
+  f.kappa = f.eps * iRs;
+  f.skappa = hl * iRs * iRs * iRs / (kB * sqrtf(den));  // sigma_MS(p*) / sqrt(den) / R*^2
   if (!isfinite(f.kappa) || !isfinite(f.skappa) || !(f.skappa > 0.f)) return f;
   f.thC0 = s0.th;
   f.RC0 = s0.RC;
@@ -238,10 +242,12 @@ __device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx
   return f;
 }
 
-__device__ __forceinline__ float kink_chi2(const TFitF& f, float R, float sg) {
+// [Phi_MS^2 sin^2(theta) + Theta_MS^2] / sigma_MS^2 of the kink model at R, with
+// isg = 1 / sigma_MS.
+__device__ __forceinline__ float kink_chi2(const TFitF& f, float R, float isg) {
   const float u = R - f.Rref;
   const float kp = f.alpha * u + f.a0p, kt = f.beta * u + f.b0p;
-  return (kp * kp * f.s2 + kt * kt) / (sg * sg);
+  return (kp * kp * f.s2 + kt * kt) * (isg * isg);
 }
 
 // ------------------------------------------------------------------ hit views
@@ -309,9 +315,10 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   const float D = sqrtf(f1.ccx * f1.ccx + f1.ccy * f1.ccy);
   o.status = 1;
   if (!(D > 0.f) || D > f1.Rct + r3 || D < fabsf(f1.Rct - r3)) return o;
-  const float a = (r3 * r3 - (f1.Rct - D) * (f1.Rct + D)) / (2.f * D);
+  const float iD = 1.f / D;
+  const float a = (r3 * r3 - (f1.Rct - D) * (f1.Rct + D)) * (0.5f * iD);
   const float hh = sqrtf(fmaxf((r3 - a) * (r3 + a), 0.f));
-  const float ux = f1.ccx / D, uy = f1.ccy / D;
+  const float ux = f1.ccx * iD, uy = f1.ccy * iD;
   const float qx0 = a * ux - hh * uy, qy0 = a * uy + hh * ux;
   const float qx1 = a * ux + hh * uy, qy1 = a * uy - hh * ux;
   // turning angle from h2 to each crossing q in the turning sense: the angle from
@@ -367,7 +374,7 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   if (!(kb != 0.f) || !isfinite(kb)) return o;
   const float Rb = 1.f / fabsf(kb);
   const float pb = C.kB * Rb;
-  const float chi2 = kink_chi2(f1, Rb, C.hl[1] / pb) + kink_chi2(f2, Rb, C.hl[2] / pb);
+  const float chi2 = kink_chi2(f1, Rb, pb * C.ihl[1]) + kink_chi2(f2, Rb, pb * C.ihl[2]);
   o.chi2 = chi2;
   o.th01 = f1.thC0 + f1.dth0 * (Rb - f1.RC0);
   if (!isfinite(chi2)) return o;

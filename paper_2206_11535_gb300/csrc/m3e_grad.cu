@@ -165,8 +165,8 @@ __device__ void fit_triplet_bwd(const float* a, const float* b, const float* c, 
   const bool ob0 = ((a[0] - c[0]) * (b[0] - c[0]) + (a[1] - c[1]) * (b[1] - c[1])) < 0.f;
   const bool ob1 = ((b[0] - a[0]) * (c[0] - a[0]) + (b[1] - a[1]) * (c[1] - a[1])) < 0.f;
   const float z01 = b[2] - a[2], z12 = c[2] - b[2];
-  const SegF s0 = segment(d01, z01, Rct, ob0);
-  const SegF s1 = segment(d12, z12, Rct, ob1);
+  const SegF s0 = segment(d01, z01, Rct, 0.5f / Rct, ob0);
+  const SegF s1 = segment(d12, z12, Rct, 0.5f / Rct, ob1);
   const float dR = s0.RC - s1.RC;
   const float alpha = 0.5f * (s0.dphi + s1.dphi);
   const float a0p = 0.5f * s1.dphi * dR;
@@ -300,13 +300,12 @@ __global__ void __launch_bounds__(GT) k_fit_grad(const __grid_constant__ DevCfg 
       if (ok) {
         const float Rb = 1.f / fabsf(kb);
         const float pb = kB * Rb;
-        chi2 = kink_chi2(f1, Rb, C.hl[1] / pb) + kink_chi2(f2, Rb, C.hl[2] / pb);
+        chi2 = kink_chi2(f1, Rb, pb * C.ihl[1]) + kink_chi2(f2, Rb, pb * C.ihl[2]);
         ok = isfinite(chi2);
         if (GRAD && ok) {
           // chi2 = sum_t (A_t^2 s2_t + B_t^2) q_t, A = alpha u + a0p, B = beta u + b0p,
           // u = Rb - Rref, q = (kB Rb / hl)^2
           const TFitF* ft[2] = {&f1, &f2};
-          const float hl[2] = {C.hl[1], C.hl[2]};
           TripBar tb[2];
           float Rb_b = 0.f;
 #pragma unroll
@@ -314,7 +313,7 @@ __global__ void __launch_bounds__(GT) k_fit_grad(const __grid_constant__ DevCfg 
             const TFitF& f = *ft[t];
             const float u = Rb - f.Rref;
             const float Aq = f.alpha * u + f.a0p, Bq = f.beta * u + f.b0p;
-            const float kq = kB * Rb / hl[t];
+            const float kq = pb * (t == 0 ? C.ihl[1] : C.ihl[2]);
             const float qt = kq * kq;
             tb[t].alpha = 2.f * Aq * u * f.s2 * qt;
             tb[t].a0p = 2.f * Aq * f.s2 * qt;

@@ -34,6 +34,7 @@ struct DevCfg {
   int col_off[4], row_off[4]; // offsets of each layer in the look-up tables
   float kB;                   // p [MeV] = kB * R [mm]
   float hl[4];                // Highland width numerator: sigma_MS(p) = hl[layer] / p
+  float ihl[4];               // 1 / hl
   float chi2_trk;
   float r3;
   float colw3;                // one layer-3 column in phi plus rounding slack (4th-hit ring search)
