@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(CTA_THREADS)
 
 // ---- stage 2: one thread per selected triplet
 template <bool DEBUG>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM: latency hiding over a few spilled registers
     k_stage2(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   const int64_t n = min((int64_t)S.counters[0], S.trip_cap);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -377,7 +377,7 @@ __device__ __forceinline__ void stage4_dump(const DevCfg& C, const KParams& P, c
 }
 
 template <bool DEBUG>
-__global__ void __launch_bounds__(S4_WARPS * 32)
+__global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 registers)
     k_stage4(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   __shared__ long long queue[S4_WARPS][64];
   long long* q = queue[threadIdx.x >> 5];
