@@ -171,6 +171,7 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
   }
   d.inv_dr01 = (float)(1.0 / (c.r_mm[1] - c.r_mm[0]));
   d.inv_dr12 = (float)(1.0 / (c.r_mm[2] - c.r_mm[1]));
+  d.dr12 = (float)(c.r_mm[2] - c.r_mm[1]);
   d.c01 = (float)(std::cos(c.phi01_max) * c.r_mm[0] * c.r_mm[1]);
   d.c12 = (float)(std::cos(c.phi12_max) * c.r_mm[1] * c.r_mm[2]);
   d.dl_max = (float)c.dlambda_max;

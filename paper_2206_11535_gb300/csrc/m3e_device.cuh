@@ -803,16 +803,17 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           sm.r12[j] = (uint16_t)r2;
           sm.c12[j] = (uint8_t)c12;
         }
-        // B: exclusive prefix of the candidate-triplet counts
-        const int nc = c01 * c12;
-        ntt += nc;
-        int ec = nc;
+        // B: exclusive prefix of the (layer-1 hit, Phi01 partner) pairs that have
+        // Phi12 partners; ntt counts their candidate triplets
+        ntt += c01 * c12;
+        const int pc = c12 ? c01 : 0;
+        int ec = pc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const int t = __shfl_up_sync(FULL, ec, o);
           if (lane >= o) ec += t;
         }
-        if (j < n1) sm.cst[j] = basec + ec - nc;
+        if (j < n1) sm.cst[j] = basec + ec - pc;
         basec += __shfl_sync(FULL, ec, 31);
       }
       if (lane == 0) sm.cst[n1] = basec;
@@ -821,43 +822,60 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
       if (sm.bad == 2) {
         npair = ntt = 0;  // the frame is counted by the stage that takes it over
       } else {
-        // C: the flat list of candidate triplets
+        // C: one lane per (layer-1 hit, Phi01 partner) pair; the lanes walk their
+        // Phi12 partners in lock step.  A z window on the layer-2 hit (the Delta
+        // lambda cut as seen from the pair, widened by 1e-3 mm against rounding)
+        // skips most partners before the exact Delta lambda and r_tc tests, which
+        // are the same expressions as in the CTA stage.
         int nt = 0;
         const int T = basec;
+        int jc = 0;
         for (int k0 = 0; k0 < T; k0 += 32) {
           const int k = k0 + lane;
-          bool pass = false;
-          int i0 = 0, i1 = 0, i2 = 0;
+          int j = jc;
+          if (k < T)
+            while (sm.cst[j + 1] <= k) ++j;  // a chunk of pairs spans few layer-1 hits
+          jc = __shfl_sync(FULL, j, 31);
+          int i0 = 0, i1 = 0, r2 = 0, c2 = 0;
+          float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f, tl01 = 0.f, zlo = 0.f, zhi = -1.f;
           if (k < T) {
-            int lo = 0, hi = n1;  // last j with cst[j] <= k
-            while (hi - lo > 1) {
-              const int mid = (lo + hi) >> 1;
-              if (sm.cst[mid] <= k) lo = mid; else hi = mid;
-            }
-            const int j = lo;
-            const int u = k - sm.cst[j];
-            const int cq = sm.c12[j];
-            const int qa = u / cq;
             i1 = l1a + j;
-            i0 = sm.p01[sm.r01[j] + qa];
-            i2 = sm.p12[sm.r12[j] + (u - qa * cq)];
-            const float x0 = sm.x[i0], y0 = sm.y[i0], x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
-            const float x2 = sm.x[i2], y2 = sm.y[i2];
-            const float dl = (sm.z[i2] - z1) * C.inv_dr12 - (z1 - sm.z[i0]) * C.inv_dr01;
-            if (fabsf(dl) <= C.dl_max) {
-              const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
-              const float cr = ax * by - ay * bx;
-              const float ex = x2 - x0, ey = y2 - y0;
-              const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
-              const float Qq = cr * cr;
-              pass = cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq;
-            }
+            i0 = sm.p01[sm.r01[j] + (k - sm.cst[j])];
+            r2 = sm.r12[j];
+            c2 = sm.c12[j];
+            x0 = sm.x[i0];
+            y0 = sm.y[i0];
+            x1 = sm.x[i1];
+            y1 = sm.y[i1];
+            z1 = sm.z[i1];
+            tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
+            zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
+            zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
           }
-          const unsigned m = __ballot_sync(FULL, pass);
-          const int kk = nt + __popc(m & ((1u << lane) - 1u));
-          if (pass && kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
-          nt += __popc(m);
-          if (nt > C.max_trip) break;  // the frame overflows: its decision is known
+          const int cmax = (int)__reduce_max_sync(FULL, (unsigned)c2);
+          for (int b = 0; b < cmax; ++b) {
+            bool pass = false;
+            int i2 = 0;
+            if (b < c2) {
+              i2 = sm.p12[r2 + b];
+              const float z2 = sm.z[i2];
+              if (z2 >= zlo && z2 <= zhi && fabsf(fmaf(z2 - z1, C.inv_dr12, -tl01)) <= C.dl_max) {
+                const float x2 = sm.x[i2], y2 = sm.y[i2];
+                const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
+                const float cr = ax * by - ay * bx;
+                const float ex = x2 - x0, ey = y2 - y0;
+                const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
+                const float Qq = cr * cr;
+                pass = cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq;
+              }
+            }
+            const unsigned m = __ballot_sync(FULL, pass);
+            const int kk = nt + __popc(m & ((1u << lane) - 1u));
+            if (pass && kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
+            nt += __popc(m);
+            if (nt > C.max_trip) break;  // the frame overflows: its decision is known
+          }
+          if (nt > C.max_trip) break;
         }
         if (lane == 0) sm.ntrip = nt;
         // npair and ntt are each lane's share (its layer-1 hits): all lanes add them
@@ -888,7 +906,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
                 const float x2 = sm.x[i2], y2 = sm.y[i2];
                 if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
                 ++ntt;
-                const float dl = (sm.z[i2] - z1) * C.inv_dr12 - tl01;
+                const float dl = fmaf(sm.z[i2] - z1, C.inv_dr12, -tl01);
                 if (!(fabsf(dl) <= C.dl_max)) continue;
                 const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
                 const float cr = ax * by - ay * bx;

@@ -26,6 +26,7 @@ constexpr int PLAIN_THREADS = 128;  // plain per-frame kernel
 struct DevCfg {
   float r[4];
   float inv_dr01, inv_dr12;   // 1/(r1 - r0), 1/(r2 - r1), nominal radii
+  float dr12;                 // r2 - r1
   float c01, c12;             // cos(phi_max) * r_i * r_j: a pair passes when h_i . h_j >= c
   float dl_max;               // |Delta lambda| <= dl_max
   float rtc_lo2, rtc_hi2;     // (2 rtc_min)^2, (2 rtc_max)^2 against (d01 d12 d20)^2 / cross^2
