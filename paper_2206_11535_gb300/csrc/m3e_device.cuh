@@ -283,6 +283,8 @@ struct GHits {
 
 // ------------------------------------------------------------------ track reconstruction
 
+constexpr int SCAN3_MAX = 96;
+
 struct TrackOut {
   int status, i3;
   float kbar, th01, chi2, mbest;
@@ -295,8 +297,9 @@ struct TrackOut {
 // both triplets at it, chi2 cut.  A kept track is written to slot `slot` of the
 // track arrays by the caller (store_track).
 //
-// Closest hit: layer-3 hits are visited by phi bin in rings around the bin of the
-// estimated point.  Every hit of ring m >= 3 lies at least (m - 2) bin widths
+// Closest hit: a frame with at most SCAN3_MAX layer-3 hits scans them all (the
+// loads are independent, so their latencies overlap); a larger one visits them
+// by phi bin in rings around the bin of the estimated point.  Every hit of ring m >= 3 lies at least (m - 2) bin widths
 // minus one column from the estimated phi (one ring of slack covers a bin index
 // rounded across an edge), so once (r3 * that)^2 exceeds the best metric no
 // farther hit can win: the search returns the same hit as a scan of all hits.
@@ -338,26 +341,34 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   int best = -1;
   float mb = FLT_MAX;
   uint32_t ab = 0;
-  for (int m = 0; m <= NB / 2; ++m) {
-    if (m >= 3) {
-      const float dmin = (float)(m - 2) * (TWO_PI_F / NB) - C.colw3;
-      if (dmin > 0.f && (r3 * dmin) * (r3 * dmin) > mb) break;
+  auto visit = [&](int j) {
+    const float dphi = wrap_pi(v.phi(j) - phi3);
+    const float dz = v.z(j) - z3;
+    const float mm = (r3 * dphi) * (r3 * dphi) + dz * dz;
+    const uint32_t aj = v.addr(j);
+    if (best < 0 || mm < mb || (mm == mb && aj < ab)) {
+      best = j;
+      mb = mm;
+      ab = aj;
     }
+  };
+  const int l3a = v.l3(0), l3e = v.l3(NB);
+  if (l3e - l3a <= SCAN3_MAX) {
+    // few layer-3 hits: a straight scan, whose loads do not depend on each other
+#pragma unroll 4
+    for (int j = l3a; j < l3e; ++j) visit(j);
+  } else {
+    for (int m = 0; m <= NB / 2; ++m) {
+      if (m >= 3) {
+        const float dmin = (float)(m - 2) * (TWO_PI_F / NB) - C.colw3;
+        if (dmin > 0.f && (r3 * dmin) * (r3 * dmin) > mb) break;
+      }
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      if (side == 1 && (m == 0 || m == NB / 2)) continue;
-      const int bb = (b3 + (side ? -m : m)) & (NB - 1);
-      const int e = v.l3(bb + 1);
-      for (int j = v.l3(bb); j < e; ++j) {
-        const float dphi = wrap_pi(v.phi(j) - phi3);
-        const float dz = v.z(j) - z3;
-        const float mm = (r3 * dphi) * (r3 * dphi) + dz * dz;
-        const uint32_t aj = v.addr(j);
-        if (best < 0 || mm < mb || (mm == mb && aj < ab)) {
-          best = j;
-          mb = mm;
-          ab = aj;
-        }
+      for (int side = 0; side < 2; ++side) {
+        if (side == 1 && (m == 0 || m == NB / 2)) continue;
+        const int bb = (b3 + (side ? -m : m)) & (NB - 1);
+        const int e = v.l3(bb + 1);
+        for (int j = v.l3(bb); j < e; ++j) visit(j);
       }
     }
   }
