@@ -45,7 +45,11 @@ struct DeviceGuard {
   }
 };
 
-constexpr int HOST_CHUNKS = 8;  // chunks of the host entry point (double-buffered)
+// Chunks of the host entry point (double-buffered): at most 4, of at least 200,000
+// frames, so that the copy of the next chunk hides behind the kernels of this one
+// while the fixed cost per chunk (launches, kernel tails) stays small.
+constexpr int HOST_CHUNKS = 4;
+constexpr int64_t HOST_CHUNK_MIN_FRAMES = 200000;
 
 }  // namespace
 
@@ -623,7 +627,8 @@ int m3e_select_frames_host(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_o
   CUDA_TRY(cudaEventRecord(x->he[0], s));
   for (int i = 0; i < 2; ++i) CUDA_TRY(cudaStreamWaitEvent(x->hs[i], x->he[0], 0));
   const int64_t total = h_off[n] - h_off[0];
-  const int nch = (int)(n < HOST_CHUNKS ? n : HOST_CHUNKS);
+  const int64_t by_size = n / HOST_CHUNK_MIN_FRAMES;
+  const int nch = (int)(by_size < 1 ? 1 : (by_size > HOST_CHUNKS ? HOST_CHUNKS : by_size));
   int64_t f0 = 0;
   int launches = 0;
   for (int k = 0; k < nch; ++k) {

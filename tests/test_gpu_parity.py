@@ -193,7 +193,9 @@ def test_small_caps_overflow_parity(m3e, cfg):
 
 
 def test_host_entry_matches_device(ctx):
-    d = gen.workload("c2", n_frames=50000, seed=12)
+    """The host entry point (copies overlapped with the kernels, four chunks at this
+    size) decides as the device entry point."""
+    d = gen.workload("c1", n_frames=850_000, seed=12)
     keep, reason = ctx.select_frames(*_dev(d))
     hh = torch.from_numpy(d["hits"]).pin_memory()
     ho = torch.from_numpy(d["off"]).pin_memory()
