@@ -892,43 +892,62 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
         // npair and ntt are each lane's share (its layer-1 hits): all lanes add them
       }
     } else {
-      // (a frame whose triplet count passed max_trip overflows whatever follows: stop)
-      for (int i1 = l1a + g.rank(); i1 < l1b; i1 += G::N) {
-        if (*(volatile int*)&sm.ntrip > C.max_trip) break;
+      // CTA stage: a warp per layer-1 hit.  The Phi01 window is walked in warp-uniform
+      // steps; for each Phi01 partner the lanes split the Phi12 window, a z window
+      // (the Delta lambda cut seen from the pair, widened by 1e-3 mm) before the exact
+      // tests, which are the warp stage's expressions.  A frame whose triplet count
+      // passed max_trip overflows whatever follows: the warps stop.
+      constexpr int NW = G::N / 32;
+      const int lane = g.rank() & 31, wid = g.rank() >> 5;
+      auto overflowed = [&]() {
+        int ov = 0;
+        if (lane == 0) ov = *(volatile int*)&sm.ntrip > C.max_trip;
+        return __shfl_sync(FULL, ov, 0) != 0;
+      };
+      for (int i1 = l1a + wid; i1 < l1b; i1 += NW) {
+        if (overflowed()) break;
         const float x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
         const int b1 = sm.bin[i1];
         const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
         const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
-        const int r0[4] = {sm.bstart[s0], sm.bstart[min(s0 + nb0, NB)], sm.bstart[0],
-                           s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : sm.bstart[0]};
-        const int r2[4] = {sm.bstart[2 * NB + s2], sm.bstart[2 * NB + min(s2 + nb2, NB)], sm.bstart[2 * NB],
-                           s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] : sm.bstart[2 * NB]};
-        npair += (r0[1] - r0[0]) + (r0[3] - r0[2]) + (r2[1] - r2[0]) + (r2[3] - r2[2]);
-#pragma unroll
-        for (int q0 = 0; q0 < 2; ++q0) {
-          for (int i0 = r0[2 * q0]; i0 < r0[2 * q0 + 1]; ++i0) {
-            const float x0 = sm.x[i0], y0 = sm.y[i0];
-            if (!(x0 * x1 + y0 * y1 >= C.c01)) continue;
-            if (*(volatile int*)&sm.ntrip > C.max_trip) break;
-            const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
-#pragma unroll
-            for (int q2 = 0; q2 < 2; ++q2) {
-              for (int i2 = r2[2 * q2]; i2 < r2[2 * q2 + 1]; ++i2) {
-                const float x2 = sm.x[i2], y2 = sm.y[i2];
-                if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
-                ++ntt;
-                const float dl = fmaf(sm.z[i2] - z1, C.inv_dr12, -tl01);
-                if (!(fabsf(dl) <= C.dl_max)) continue;
-                const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
-                const float cr = ax * by - ay * bx;
-                const float ex = x2 - x0, ey = y2 - y0;
-                const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
-                const float Qq = cr * cr;
-                if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
-                const int k = atomicAdd(&sm.ntrip, 1);
-                if (k < CT) sm.u.trip[k] = make_trip<typename S::TripT>(i0, i1, i2);
-              }
-            }
+        const int a0 = sm.bstart[s0], n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
+        const int n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
+        const int a2 = sm.bstart[2 * NB + s2], n2a = sm.bstart[2 * NB + min(s2 + nb2, NB)] - a2;
+        const int w2 = sm.bstart[2 * NB];
+        const int n2w = n2a + (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - w2 : 0);
+        if (lane == 0) npair += n0w + n2w;
+        int c12 = 0;  // Phi12 partners of this hit: the candidate count is c01 * c12
+        if (stats) {
+          for (int k = lane; k < n2w; k += 32) {
+            const int i2 = k < n2a ? a2 + k : w2 + (k - n2a);
+            c12 += x1 * sm.x[i2] + y1 * sm.y[i2] >= C.c12;
+          }
+          c12 = (int)__reduce_add_sync(FULL, (unsigned)c12);
+        }
+        for (int k0 = 0; k0 < n0w; ++k0) {
+          const int i0 = k0 < n0a ? a0 + k0 : k0 - n0a;
+          const float x0 = sm.x[i0], y0 = sm.y[i0];
+          if (!(x0 * x1 + y0 * y1 >= C.c01)) continue;  // warp-uniform
+          if (lane == 0) ntt += c12;
+          if (overflowed()) break;
+          const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
+          const float zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
+          const float zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
+          for (int k = lane; k < n2w; k += 32) {
+            const int i2 = k < n2a ? a2 + k : w2 + (k - n2a);
+            const float z2 = sm.z[i2];
+            if (!(z2 >= zlo && z2 <= zhi)) continue;
+            const float x2 = sm.x[i2], y2 = sm.y[i2];
+            if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
+            if (!(fabsf(fmaf(z2 - z1, C.inv_dr12, -tl01)) <= C.dl_max)) continue;
+            const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
+            const float cr = ax * by - ay * bx;
+            const float ex = x2 - x0, ey = y2 - y0;
+            const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
+            const float Qq = cr * cr;
+            if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
+            const int kk = atomicAdd(&sm.ntrip, 1);
+            if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
           }
         }
       }
