@@ -924,30 +924,41 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           }
           c12 = (int)__reduce_add_sync(FULL, (unsigned)c12);
         }
-        for (int k0 = 0; k0 < n0w; ++k0) {
-          const int i0 = k0 < n0a ? a0 + k0 : k0 - n0a;
-          const float x0 = sm.x[i0], y0 = sm.y[i0];
-          if (!(x0 * x1 + y0 * y1 >= C.c01)) continue;  // warp-uniform
-          if (lane == 0) ntt += c12;
-          if (overflowed()) break;
-          const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
-          const float zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
-          const float zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
-          for (int k = lane; k < n2w; k += 32) {
-            const int i2 = k < n2a ? a2 + k : w2 + (k - n2a);
-            const float z2 = sm.z[i2];
-            if (!(z2 >= zlo && z2 <= zhi)) continue;
-            const float x2 = sm.x[i2], y2 = sm.y[i2];
-            if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
-            if (!(fabsf(fmaf(z2 - z1, C.inv_dr12, -tl01)) <= C.dl_max)) continue;
-            const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
-            const float cr = ax * by - ay * bx;
-            const float ex = x2 - x0, ey = y2 - y0;
-            const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
-            const float Qq = cr * cr;
-            if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
-            const int kk = atomicAdd(&sm.ntrip, 1);
-            if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
+        bool stop = false;
+        for (int kb = 0; kb < n0w && !stop; kb += 32) {
+          // the lanes test 32 of the Phi01 window at once; the warp walks the partners
+          int i0l = 0;
+          bool p01 = false;
+          if (kb + lane < n0w) {
+            i0l = kb + lane < n0a ? a0 + kb + lane : kb + lane - n0a;
+            p01 = sm.x[i0l] * x1 + sm.y[i0l] * y1 >= C.c01;
+          }
+          unsigned mp = __ballot_sync(FULL, p01);
+          if (lane == 0) ntt += __popc(mp) * c12;
+          stop = overflowed();
+          while (mp && !stop) {
+            const int i0 = __shfl_sync(FULL, i0l, __ffs(mp) - 1);
+            mp &= mp - 1;
+            const float x0 = sm.x[i0], y0 = sm.y[i0];
+            const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
+            const float zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
+            const float zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
+            for (int k = lane; k < n2w; k += 32) {
+              const int i2 = k < n2a ? a2 + k : w2 + (k - n2a);
+              const float z2 = sm.z[i2];
+              if (!(z2 >= zlo && z2 <= zhi)) continue;
+              const float x2 = sm.x[i2], y2 = sm.y[i2];
+              if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
+              if (!(fabsf(fmaf(z2 - z1, C.inv_dr12, -tl01)) <= C.dl_max)) continue;
+              const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
+              const float cr = ax * by - ay * bx;
+              const float ex = x2 - x0, ey = y2 - y0;
+              const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
+              const float Qq = cr * cr;
+              if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
+              const int kk = atomicAdd(&sm.ntrip, 1);
+              if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
+            }
           }
         }
       }
