@@ -34,7 +34,12 @@ WORKLOAD = ("full-rate throughput: 1,000,000 frames per GPU, Poisson(20) tracks/
             "4 layers r=25/31/73/85 mm, B=1 T, 80 um pixels, int32 addresses")
 # Arithmetic operations per work item of the method's formulas (FMA = 2, each
 # transcendental, division or square root = 1), grouped by the stage kernel that
-# does the work; see DESIGN.md "Roofline".
+# does the work: a Phi pair test is a dot product and a compare (4); a candidate
+# triplet the Delta lambda difference and compare (6); a selected triplet two
+# triplet fits (~190 each), the layer-3 extrapolation and search and the global
+# fit (~460); an energy test three additions and a compare (7); a combination the
+# vertex prefilter (75); a vertexed one the intersections, closest points, chi2
+# and cuts (565).  The work items are counted by the library's statistics.
 STAGE_OPS = {  # name: (indices into m3e_stage_times, ops per counted item)
     "stage1 decode+sort+cuts (warp and CTA tiers)": ((0, 1, 2), {"pair_tests": 4, "triplet_tests": 6}),
     "stage2 track fits": ((3,), {"triplets": 460}),
