@@ -321,10 +321,7 @@ void free_scratch(Scratch& sc) {
 SParams staged_params(const Scratch& sc) {
   SParams s{};
   const int64_t H = sc.hits_cap, F = sc.frames_cap;
-  s.hx = sc.hf;
-  s.hy = sc.hf + H;
-  s.hz = sc.hf + 2 * H;
-  s.hphi = sc.hf + 3 * H;
+  s.hp = reinterpret_cast<float4*>(sc.hf);
   s.haddr = sc.haddr;
   s.hidx = sc.hidx;
   s.l3 = sc.l3;

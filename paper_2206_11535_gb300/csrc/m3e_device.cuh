@@ -255,28 +255,20 @@ __device__ __forceinline__ float kink_chi2(const TFitF& f, float R, float isg) {
 // Hits of one frame, sorted by (layer, phi bin), as build_track reads them: from
 // the shared-memory stage of a fused kernel, or from global memory in the staged
 // form (pointers already offset to the frame).
+// pos(i) = (x, y, z, phi) of sorted hit i.
 template <class S>
 struct SmHits {
   const S& s;
-  __device__ __forceinline__ float x(int i) const { return s.x[i]; }
-  __device__ __forceinline__ float y(int i) const { return s.y[i]; }
-  __device__ __forceinline__ float z(int i) const { return s.z[i]; }
-  __device__ __forceinline__ float phi(int i) const { return s.phi[i]; }
+  __device__ __forceinline__ float4 pos(int i) const { return make_float4(s.x[i], s.y[i], s.z[i], s.phi[i]); }
   __device__ __forceinline__ uint32_t addr(int i) const { return s.addr[i]; }
   __device__ __forceinline__ int l3(int b) const { return s.bstart[3 * NB + b]; }  // layer-3 bin starts
 };
 
-struct GHits {
-  const float* __restrict__ xs;
-  const float* __restrict__ ys;
-  const float* __restrict__ zs;
-  const float* __restrict__ ps;
+struct GHits {                       // one 16-byte load per hit
+  const float4* __restrict__ ps;
   const uint32_t* __restrict__ as;
   const uint16_t* __restrict__ l3s;  // NB + 1 layer-3 bin starts, frame-relative
-  __device__ __forceinline__ float x(int i) const { return __ldg(xs + i); }
-  __device__ __forceinline__ float y(int i) const { return __ldg(ys + i); }
-  __device__ __forceinline__ float z(int i) const { return __ldg(zs + i); }
-  __device__ __forceinline__ float phi(int i) const { return __ldg(ps + i); }
+  __device__ __forceinline__ float4 pos(int i) const { return __ldg(ps + i); }
   __device__ __forceinline__ uint32_t addr(int i) const { return __ldg(as + i); }
   __device__ __forceinline__ int l3(int b) const { return __ldg(l3s + b); }
 };
@@ -309,9 +301,10 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   o.status = 0;
   o.i3 = -1;
   o.kbar = o.th01 = o.chi2 = o.mbest = 0.f;
-  const float x0 = v.x(i0), y0 = v.y(i0), z0 = v.z(i0);
-  const float x1 = v.x(i1), y1 = v.y(i1), z1 = v.z(i1);
-  const float x2 = v.x(i2), y2 = v.y(i2), z2 = v.z(i2);
+  const float4 p0 = v.pos(i0), p1 = v.pos(i1), p2 = v.pos(i2);
+  const float x0 = p0.x, y0 = p0.y, z0 = p0.z;
+  const float x1 = p1.x, y1 = p1.y, z1 = p1.z;
+  const float x2 = p2.x, y2 = p2.y, z2 = p2.z;
   const TFitF f1 = fit_triplet(x0, y0, z0, x1, y1, z1, x2, y2, z2, C.hl[1], C.kB);
   if (!f1.valid) return o;
   const float r3 = C.r3;
@@ -342,8 +335,9 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   float mb = FLT_MAX;
   uint32_t ab = 0;
   auto visit = [&](int j) {
-    const float dphi = wrap_pi(v.phi(j) - phi3);
-    const float dz = v.z(j) - z3;
+    const float4 q = v.pos(j);
+    const float dphi = wrap_pi(q.w - phi3);
+    const float dz = q.z - z3;
     const float mm = (r3 * dphi) * (r3 * dphi) + dz * dz;
     const uint32_t aj = v.addr(j);
     if (best < 0 || mm < mb || (mm == mb && aj < ab)) {
@@ -376,7 +370,8 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   if (best < 0) return o;
   o.i3 = best;
   o.mbest = mb;
-  const TFitF f2 = fit_triplet(x1, y1, z1, x2, y2, z2, v.x(best), v.y(best), v.z(best), C.hl[2], C.kB);
+  const float4 p3 = v.pos(best);
+  const TFitF f2 = fit_triplet(x1, y1, z1, x2, y2, z2, p3.x, p3.y, p3.z, C.hl[2], C.kB);
   o.status = 3;
   if (!f2.valid) return o;
   const float w1 = 1.f / (f1.skappa * f1.skappa), w2 = 1.f / (f2.skappa * f2.skappa);

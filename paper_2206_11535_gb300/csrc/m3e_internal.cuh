@@ -69,7 +69,7 @@ struct KParams {
 
 // Global scratch of the staged form (see m3e_staged.cu), sized per batch.
 struct SParams {
-  float *hx, *hy, *hz, *hphi;  // sorted hits of the pending frames (from the hit allocator)
+  float4* hp;                  // sorted hits of the pending frames (from the hit allocator): x, y, z, phi
   uint32_t* haddr;
   uint16_t* hidx;              // input index of each sorted hit (candidate record only)
   long long* fhbase;           // per frame: first sorted hit

@@ -59,15 +59,14 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, 
     return false;
   }
   for (int i = g.rank(); i < n; i += G::N) {
-    S.hx[hb + i] = sm.x[i];
-    S.hy[hb + i] = sm.y[i];
-    S.hz[hb + i] = sm.z[i];
+    float phi;
     if constexpr (Sm::kPhi) {
-      S.hphi[hb + i] = sm.phi[i];
+      phi = sm.phi[i];
     } else {
       const Dec d = decode(C, sm.addr[i]);
-      S.hphi[hb + i] = __ldg(P.col_lut + C.col_off[d.L] + d.g).z;
+      phi = __ldg(P.col_lut + C.col_off[d.L] + d.g).z;
     }
+    S.hp[hb + i] = make_float4(sm.x[i], sm.y[i], sm.z[i], phi);
     S.haddr[hb + i] = sm.addr[i];
     if constexpr (DEBUG) {
       static_assert(Sm::kIdx, "the candidate record needs the input indices");
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM: latency hiding over
     const int f = r.x;
     if (f < 0) continue;
     const int64_t base = S.fhbase[f];
-    const GHits v{S.hx + base, S.hy + base, S.hz + base, S.hphi + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
+    const GHits v{S.hp + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
     float tk[14];
     const TrackOut o = build_track(v, C, r.y, r.z, r.w, tk);
     S.tstatus[i] = (uint8_t)o.status;
