@@ -75,7 +75,7 @@ struct FrameSm {
     TripT trip[CT];             // selected triplets (sorted-hit indices)
     uint32_t combo[CC];         // e+ e+ e- combinations (track indices), after the fits
   } u;
-  int ntrip, npos, nneg, ncombo, flag, bad;
+  int ntrip, npos, nneg, ncombo, nstore, flag, bad;
   unsigned long long acc[ST_REASON0 + 8];  // statistics of this group's frames
   unsigned long long facc[ST_REASON0];     // statistics of the current frame
 };
@@ -483,6 +483,22 @@ __device__ __forceinline__ float target_distance(const DevCfg& C, float x, float
   return sqrtf(dx * dx + dz * dz);
 }
 
+// Longitudinal momentum sum of a combination (the z part of |sum p|, Sec. "Vertex
+// Fit"), rounded in one fixed order, so that the vertex and the early test below
+// see the same value.  It does not depend on the vertex position.
+__device__ __forceinline__ float pz_track(float p, float ct) { return __fmul_rn(p, ct); }
+__device__ __forceinline__ float pz_sum(float pa, float pb, float pe) { return __fadd_rn(__fadd_rn(pa, pb), pe); }
+
+// |sum p| >= |P_z|: the vertex's sum of squares only adds non-negative terms and
+// rounding is monotone, so its |sum p| is at least sqrt(fl(P_z^2)).  When P_z^2
+// exceeds the squared momentum cut by a relative 1e-4 (far more than any rounding
+// of the cut or the square root), the combination fails the cut whatever its
+// vertex, and the decision-only runs skip its vertex.  Runs that report each
+// combination's status (debug records, statistics) still fit it.
+__device__ __forceinline__ bool pz_fails_ptot(float Pz, float ptot_max) {
+  return __fmul_rn(Pz, Pz) > ptot_max * ptot_max * 1.0001f;
+}
+
 struct VtxOut {
   int status, pass;
   float chi2, tdist, ptot;
@@ -621,7 +637,7 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
   o.status = 2;
   o.chi2 = best;
   o.tdist = target_distance(C, bmx, bmy, bmz);
-  float Px = 0.f, Py = 0.f, Pz = 0.f;
+  float Px = 0.f, Py = 0.f;
   const TrackR* V[3] = {&A, &B, &E};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -632,8 +648,8 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
     const float pt = t.p * t.st;
     Px += pt * t.eps * uy;
     Py -= pt * t.eps * ux;
-    Pz += t.p * t.ct;
   }
+  const float Pz = pz_sum(pz_track(A.p, A.ct), pz_track(B.p, B.ct), pz_track(E.p, E.ct));
   o.ptot = sqrtf(Px * Px + Py * Py + Pz * Pz);
   o.pass = o.chi2 <= C.vtx_chi2 && o.tdist <= C.tgt_dist && o.ptot <= C.ptot_max;
   return o;
@@ -704,6 +720,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     sm.npos = 0;
     sm.nneg = 0;
     sm.ncombo = 0;
+    sm.nstore = 0;
     sm.flag = 0;
     if (stats)
       for (int k = 0; k < ST_REASON0; ++k) sm.facc[k] = 0;
@@ -1017,7 +1034,10 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
   if (stats && g.leader()) sm.facc[ST_TRK] += ntrk;
 
   // ---- E: energy test of every (e+ pair, e-) combination (Algorithm 4, part 1):
-  // one e+ pair per thread, the e- loop uniform across the group (broadcast reads)
+  // one e+ pair per thread, the e- loop uniform across the group (broadcast reads).
+  // All passing combinations count towards the cap; a decision-only run stores only
+  // those whose P_z leaves the momentum cut open (pz_fails_ptot).
+  const bool prune = !DEBUG && !stats;
   {
     const int npair = npos * (npos - 1) / 2;
     for (int pr = g.rank(); pr < npair; pr += G::N) {
@@ -1026,12 +1046,19 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
       while ((b + 1) * b / 2 <= pr) ++b;
       const int a = pr - b * (b - 1) / 2;
       const float eab = sm.t.E[a] + sm.t.E[b];
+      const float pzab = __fadd_rn(pz_track(sm.t.p[a], sm.t.ct[a]), pz_track(sm.t.p[b], sm.t.ct[b]));
       for (int c = 0; c < nneg; ++c) {
         const int ci = CK - 1 - c;
         const float e = (eab + sm.t.E[ci]) - C.m_mu;
         if (fabsf(e) <= C.e_win) {
           const int k = atomicAdd(&sm.ncombo, 1);
-          if (k < CC) sm.u.combo[k] = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)ci << 16);
+          const uint32_t code = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)ci << 16);
+          if (!prune) {
+            if (k < CC) sm.u.combo[k] = code;
+          } else if (!pz_fails_ptot(__fadd_rn(pzab, pz_track(sm.t.p[ci], sm.t.ct[ci])), C.ptot_max)) {
+            const int k2 = atomicAdd(&sm.nstore, 1);
+            if (k2 < CC) sm.u.combo[k2] = code;
+          }
         }
       }
     }
@@ -1039,18 +1066,19 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
   }
   g.sync();
   const int ncombo = sm.ncombo;
+  const int nvtx = prune ? sm.nstore : ncombo;  // combinations to fit
   if (DEBUG && g.leader()) P.dump.n_combo[f] = ncombo;
   if (ncombo > C.max_combo) return M3E_COMBO_OVERFLOW;
-  if (DEFER && ncombo > CC) return DEFERRED;
+  if (DEFER && nvtx > CC) return DEFERRED;
   if (stats && g.leader()) sm.facc[ST_COMBO] += ncombo;
 
   // ---- F: vertex of each combination (Algorithm 4, part 2), early exit
   bool found = false;
   unsigned nv = 0;
-  for (int c0 = 0; c0 < ncombo; c0 += G::N) {
+  for (int c0 = 0; c0 < nvtx; c0 += G::N) {
     const int c = c0 + g.rank();
     bool pass = false;
-    if (c < ncombo) {
+    if (c < nvtx) {
       const uint32_t cb = sm.u.combo[c];
       const int a = cb & 255, b = (cb >> 8) & 255, e = (cb >> 16) & 255;
       const VtxOut v = vertex(load_track(sm.t, a), load_track(sm.t, b), load_track(sm.t, e), C);

@@ -28,6 +28,7 @@ constexpr int S3_WARPS = 4;
 struct S3Sm {                                      // stage 3, per warp
   int pidx[C_TRK], nidx[C_TRK];                    // triplet index of each e+ / e- track
   float pE[C_TRK], nE[C_TRK];
+  float pPz[C_TRK], nPz[C_TRK];                    // p cos(theta) of each track
   int npos, nneg;
   unsigned long long acc[ST_REASON0 + 8];
 };
@@ -231,11 +232,12 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
       for (int t0 = 0; t0 < nt; t0 += 32) {
         const int t = t0 + lane;
         const bool kept = t < nt && S.tstatus[tb + t] == 5;
-        float eps = 0.f, E = 0.f;
+        float eps = 0.f, E = 0.f, pz = 0.f;
         if (kept) {
           const float4 q1 = __ldg(S.trec + 4 * (int64_t)(tb + t) + 1);
           const float4 q3 = __ldg(S.trec + 4 * (int64_t)(tb + t) + 3);
           E = q1.w;
+          pz = pz_track(q1.z, q1.x);
           eps = q3.y;
         }
         const bool pos = kept && eps > 0.f, neg = kept && !(eps > 0.f);
@@ -244,10 +246,12 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
         if (pos && kp < C_TRK) {
           sm.pidx[kp] = tb + t;
           sm.pE[kp] = E;
+          sm.pPz[kp] = pz;
         }
         if (neg && kn < C_TRK) {
           sm.nidx[kn] = tb + t;
           sm.nE[kn] = E;
+          sm.nPz[kn] = pz;
         }
         __syncwarp();
       }
@@ -256,35 +260,44 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
       int r = PENDING;
       if (npos + nneg > C.max_trk) r = M3E_TRACK_OVERFLOW;
       const int npair = npos * (npos - 1) / 2;
-      int ncombo = 0;
+      // all energy-test survivors count towards the cap; a decision-only run
+      // writes only those whose P_z leaves the momentum cut open (pz_fails_ptot)
+      const bool prune = !DEBUG && !stats;
+      int ncombo = 0, nwrite = 0;
       if (r == PENDING) {
         if (stats && lane == 0) {
           sm.acc[ST_TRK] += npos + nneg;
           sm.acc[ST_ETEST] += (unsigned long long)npair * nneg;
         }
-        // pass 1: count the combinations passing the energy test
+        // pass 1: count the combinations passing the energy test, and those to write
         for (int p0 = 0; p0 < npair; p0 += 32) {
           const int pr = p0 + lane;
-          int cnt = 0;
+          int cnt = 0, cw = 0;
           if (pr < npair) {
             int b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
             while (b * (b - 1) / 2 > pr) --b;
             while ((b + 1) * b / 2 <= pr) ++b;
             const int a = pr - b * (b - 1) / 2;
             const float eab = sm.pE[a] + sm.pE[b];
-            for (int c = 0; c < nneg; ++c) cnt += fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
+            const float pzab = __fadd_rn(sm.pPz[a], sm.pPz[b]);
+            for (int c = 0; c < nneg; ++c) {
+              const bool e_ok = fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
+              cnt += e_ok;
+              cw += e_ok && !(prune && pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max));
+            }
           }
           ncombo += __reduce_add_sync(FULL, cnt);
+          nwrite += __reduce_add_sync(FULL, cw);
         }
         if (DEBUG && lane == 0) P.dump.n_combo[f] = ncombo;
         if (ncombo > C.max_combo) r = M3E_COMBO_OVERFLOW;
-        else if (ncombo == 0) r = M3E_DROP;
+        else if (nwrite == 0) r = M3E_DROP;  // no combination, or none that can pass
       }
       if (r == PENDING) {
         long long cb = 0;
-        if (lane == 0) cb = (long long)atomicAdd(&S.counters[1], (unsigned long long)ncombo);
+        if (lane == 0) cb = (long long)atomicAdd(&S.counters[1], (unsigned long long)nwrite);
         cb = __shfl_sync(FULL, cb, 0);
-        if (cb + ncombo > S.combo_cap) {
+        if (cb + nwrite > S.combo_cap) {
           for (int64_t t = cb + lane; t < S.combo_cap; t += 32) S.combo[t] = make_int4(-1, 0, 0, 0);
           r = DEFERRED;
         } else {
@@ -293,7 +306,7 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
           for (int p0 = 0; p0 < npair; p0 += 32) {
             const int pr = p0 + lane;
             int a = 0, b = 0;
-            float eab = 0.f;
+            float eab = 0.f, pzab = 0.f;
             const bool act = pr < npair;
             if (act) {
               b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
@@ -301,9 +314,11 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
               while ((b + 1) * b / 2 <= pr) ++b;
               a = pr - b * (b - 1) / 2;
               eab = sm.pE[a] + sm.pE[b];
+              pzab = __fadd_rn(sm.pPz[a], sm.pPz[b]);
             }
             for (int c = 0; c < nneg; ++c) {
-              const bool pass = act && fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
+              const bool pass = act && fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win &&
+                                !(prune && pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max));
               const unsigned m = __ballot_sync(FULL, pass);
               if (pass) S.combo[w + __popc(m & ((1u << lane) - 1u))] = make_int4(f, sm.pidx[a], sm.pidx[b], sm.nidx[c]);
               w += __popc(m);
@@ -311,7 +326,7 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
           }
           if (lane == 0) {
             S.fcbase[f] = cb;
-            S.fncombo[f] = ncombo;
+            S.fncombo[f] = nwrite;
             if (stats) sm.acc[ST_COMBO] += ncombo;
           }
         }

@@ -288,3 +288,26 @@ def test_high_rate_sample(ctx, ocfg):
     for form in ("fused", "plain"):
         rf = _np(ctx.select_frames_debug(hits, off, cap_trip=1024, cap_combo=1024, form=FORMS[form]))
         assert (rf["reason"] == rec["reason"]).all()
+
+
+@pytest.mark.parametrize("workload", ["c1", "c2", "signal"])
+def test_momentum_bound_keeps_the_decisions(ctx, m3e, cfg, workload):
+    """Decision-only runs skip the vertex of combinations whose longitudinal
+    momentum alone fails the |sum p| cut; runs with statistics or debug records fit
+    every combination.  All of them decide every frame alike, in every form."""
+    if workload == "signal":
+        d = gen.generate(3000, 10.0, 0.5, 1, seed=71)  # a signal decay in every frame
+    else:
+        d = gen.workload(workload, n_frames=3000, seed=71)
+    hits, off = _dev(d)
+    ref = ctx.select_frames(hits, off, stats=m3e.new_stats())[1].cpu().numpy()
+    assert (ref == m3e.VERTEX).sum() > (1000 if workload == "signal" else 0)
+    for form, entry in (("staged", ctx.select_frames), ("fused", ctx.select_frames_fused),
+                        ("plain", ctx.select_frames_plain)):
+        assert (entry(hits, off)[1].cpu().numpy() == ref).all(), form
+    rec = _np(ctx.select_frames_debug(hits, off, form=FORMS["staged"]))
+    assert (rec["reason"] == ref).all()
+    # the bound is active: most fitted combinations fail the momentum cut
+    st = rec["combo"][..., 3]
+    fitted = (st & 255) == 2
+    assert (rec["combo_val"][..., 3][fitted] > cfg["cuts"]["ptot_max"]).mean() > 0.5
