@@ -37,14 +37,16 @@ WORKLOAD = ("full-rate throughput: 1,000,000 frames per GPU, Poisson(20) tracks/
 # does the work: a Phi pair test is a dot product and a compare (4); a candidate
 # triplet the Delta lambda difference and compare (6); a selected triplet two
 # triplet fits (~190 each), the layer-3 extrapolation and search and the global
-# fit (~460); an energy test three additions and a compare (7); a combination the
-# vertex prefilter (75); a vertexed one the intersections, closest points, chi2
-# and cuts (565).  The work items are counted by the library's statistics.
+# fit (~460); an energy test three additions and a compare (7); a combination
+# passing it the longitudinal momentum bound (3); a combination whose P_z leaves
+# the momentum cut open the vertex prefilter (75) and, if vertexed, the
+# intersections, closest points, chi2 and cuts (565).  The work items are counted
+# by the library's statistics (a timed run evaluates no other vertex).
 STAGE_OPS = {  # name: (indices into m3e_stage_times, ops per counted item)
     "stage1 decode+sort+cuts (warp and CTA tiers)": ((0, 1, 2), {"pair_tests": 4, "triplet_tests": 6}),
     "stage2 track fits": ((3,), {"triplets": 460}),
-    "stage3 energy test": ((4,), {"energy_tests": 7}),
-    "stage4 vertex": ((5,), {"combos": 75, "vertexed": 565}),
+    "stage3 energy test": ((4,), {"energy_tests": 7, "combos": 3}),
+    "stage4 vertex": ((5,), {"pz_open": 75, "vertexed_pz_open": 565}),
     "stage5 decision": ((6,), {}),
 }
 

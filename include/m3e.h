@@ -106,6 +106,10 @@ typedef struct {
   unsigned long long combos;         /* combinations passing the energy test */
   unsigned long long vertexed;       /* combinations vertexed */
   unsigned long long deferred;       /* frames re-run by the large-frame path */
+  unsigned long long pz_open;        /* combinations whose longitudinal momentum sum alone does not
+                                        fail the |sum p| cut: the only ones whose vertex a run
+                                        without statistics or candidate record evaluates */
+  unsigned long long vertexed_pz_open; /* vertexed combinations among those */
   unsigned long long reasons[8];     /* frames per m3e_reason */
 } m3e_stats;
 

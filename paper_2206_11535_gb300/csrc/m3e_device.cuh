@@ -811,24 +811,41 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
         base0 += __shfl_sync(FULL, e0, 31);
         base2 += __shfl_sync(FULL, e2, 31);
         over = over || base0 > W_P01 || base2 > W_P12;
-        int c01 = 0, c12 = 0;
+        int c01 = 0, c12 = 0, c12all = 0;
         if (j < n1 && !over) {
+          const float z1 = sm.z[i1];
+          float tlmin = FLT_MAX, tlmax = -FLT_MAX;
           for (int k = 0; k < n0w; ++k) {
             const int i0 = k < n0a ? a0 + k : k - n0a;
-            if (sm.x[i0] * x1 + sm.y[i0] * y1 >= C.c01) sm.p01[r0 + c01++] = (uint8_t)i0;
+            if (sm.x[i0] * x1 + sm.y[i0] * y1 >= C.c01) {
+              sm.p01[r0 + c01++] = (uint8_t)i0;
+              const float tl = (z1 - sm.z[i0]) * C.inv_dr01;
+              tlmin = fminf(tlmin, tl);
+              tlmax = fmaxf(tlmax, tl);
+            }
           }
-          if (c01)
+          if (c01) {
+            // a Phi12 partner is stored only inside the union of its pairs' z windows
+            // (part C), spanned by the smallest and largest tan(lambda01) of the
+            // Phi01 partners; c12all counts them all for the statistics
+            const float zlo = z1 + (tlmin - C.dl_max) * C.dr12 - 1e-3f;
+            const float zhi = z1 + (tlmax + C.dl_max) * C.dr12 + 1e-3f;
             for (int k = 0; k < n2w; ++k) {
               const int i2 = k < n2a ? a2 + k : sm.bstart[2 * NB] + (k - n2a);
-              if (x1 * sm.x[i2] + y1 * sm.y[i2] >= C.c12) sm.p12[r2 + c12++] = (uint8_t)i2;
+              if (x1 * sm.x[i2] + y1 * sm.y[i2] >= C.c12) {
+                ++c12all;
+                const float z2 = sm.z[i2];
+                if (z2 >= zlo && z2 <= zhi) sm.p12[r2 + c12++] = (uint8_t)i2;
+              }
             }
+          }
           sm.r01[j] = (uint16_t)r0;
           sm.r12[j] = (uint16_t)r2;
           sm.c12[j] = (uint8_t)c12;
         }
         // B: exclusive prefix of the (layer-1 hit, Phi01 partner) pairs that have
         // Phi12 partners; ntt counts their candidate triplets
-        ntt += c01 * c12;
+        ntt += c01 * c12all;
         const int pc = c12 ? c01 : 0;
         int ec = pc;
 #pragma unroll
@@ -1053,9 +1070,11 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
         if (fabsf(e) <= C.e_win) {
           const int k = atomicAdd(&sm.ncombo, 1);
           const uint32_t code = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)ci << 16);
+          const bool open = !pz_fails_ptot(__fadd_rn(pzab, pz_track(sm.t.p[ci], sm.t.ct[ci])), C.ptot_max);
           if (!prune) {
             if (k < CC) sm.u.combo[k] = code;
-          } else if (!pz_fails_ptot(__fadd_rn(pzab, pz_track(sm.t.p[ci], sm.t.ct[ci])), C.ptot_max)) {
+            if (stats && open) atomicAdd(&sm.facc[ST_PZOPEN], 1ull);
+          } else if (open) {
             const int k2 = atomicAdd(&sm.nstore, 1);
             if (k2 < CC) sm.u.combo[k2] = code;
           }
@@ -1068,13 +1087,16 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
   const int ncombo = sm.ncombo;
   const int nvtx = prune ? sm.nstore : ncombo;  // combinations to fit
   if (DEBUG && g.leader()) P.dump.n_combo[f] = ncombo;
-  if (ncombo > C.max_combo) return M3E_COMBO_OVERFLOW;
+  if (ncombo > C.max_combo) {
+    if (stats && g.leader()) sm.facc[ST_PZOPEN] = 0;  // counted, as the combinations, only when fitted
+    return M3E_COMBO_OVERFLOW;
+  }
   if (DEFER && nvtx > CC) return DEFERRED;
   if (stats && g.leader()) sm.facc[ST_COMBO] += ncombo;
 
   // ---- F: vertex of each combination (Algorithm 4, part 2), early exit
   bool found = false;
-  unsigned nv = 0;
+  unsigned nv = 0, nvo = 0;
   for (int c0 = 0; c0 < nvtx; c0 += G::N) {
     const int c = c0 + g.rank();
     bool pass = false;
@@ -1084,6 +1106,9 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
       const VtxOut v = vertex(load_track(sm.t, a), load_track(sm.t, b), load_track(sm.t, e), C);
       pass = v.pass != 0;
       nv += v.status == 2;
+      if (stats && v.status == 2)
+        nvo += !pz_fails_ptot(pz_sum(pz_track(sm.t.p[a], sm.t.ct[a]), pz_track(sm.t.p[b], sm.t.ct[b]),
+                                     pz_track(sm.t.p[e], sm.t.ct[e])), C.ptot_max);
       if (DEBUG && c < P.dump.cap_combo) {
         const int64_t r = (int64_t)f * P.dump.cap_combo + c;
         P.dump.combo[4 * r + 0] = sm.t.tid[a];
@@ -1100,6 +1125,7 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
     if (found && !DEBUG) break;
   }
   if (stats && nv) atomicAdd(&sm.facc[ST_VTX], (unsigned long long)nv);
+  if (stats && nvo) atomicAdd(&sm.facc[ST_VTXOPEN], (unsigned long long)nvo);
   return found ? M3E_VERTEX : M3E_DROP;
 }
 

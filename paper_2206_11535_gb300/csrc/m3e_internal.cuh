@@ -90,7 +90,7 @@ struct SParams {
 };
 
 enum { ST_FRAMES = 0, ST_HITS, ST_PAIRS, ST_TTESTS, ST_TRIP, ST_TRK, ST_ETEST, ST_COMBO, ST_VTX, ST_DEFER,
-       ST_REASON0 };
+       ST_PZOPEN, ST_VTXOPEN, ST_REASON0 };
 
 enum { ERR_BADHIT = 1, ERR_NEGSIZE = 2 };
 

@@ -24,11 +24,13 @@ constexpr int M_HITS = 1024;                       // stage-1 middle tier (CTA p
 using SmFrontMid = FrameSm<M_HITS, C_TRIP, 1, 1>;
 using SmFrontCta = FrameSm<C_HITS, C_TRIP, 1, 1>;
 constexpr int S3_WARPS = 4;
+constexpr int S3_BUF = 128;  // combinations a frame of stage 3 collects before writing
 
 struct S3Sm {                                      // stage 3, per warp
   int pidx[C_TRK], nidx[C_TRK];                    // triplet index of each e+ / e- track
   float pE[C_TRK], nE[C_TRK];
   float pPz[C_TRK], nPz[C_TRK];                    // p cos(theta) of each track
+  uint32_t wbuf[S3_BUF];                           // combinations to write: a | b << 8 | c << 16
   int npos, nneg;
   unsigned long long acc[ST_REASON0 + 8];
 };
@@ -263,32 +265,43 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
       // all energy-test survivors count towards the cap; a decision-only run
       // writes only those whose P_z leaves the momentum cut open (pz_fails_ptot)
       const bool prune = !DEBUG && !stats;
-      int ncombo = 0, nwrite = 0;
+      int ncombo = 0, nwrite = 0, nopen = 0;
       if (r == PENDING) {
         if (stats && lane == 0) {
           sm.acc[ST_TRK] += npos + nneg;
           sm.acc[ST_ETEST] += (unsigned long long)npair * nneg;
         }
-        // pass 1: count the combinations passing the energy test, and those to write
+        // one pass over the (e+ pair, e-) combinations: count those passing the energy
+        // test and collect those to write, in (pair, e-) order, in the warp's buffer
         for (int p0 = 0; p0 < npair; p0 += 32) {
           const int pr = p0 + lane;
-          int cnt = 0, cw = 0;
-          if (pr < npair) {
-            int b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
+          const bool act = pr < npair;
+          int a = 0, b = 0;
+          float eab = 0.f, pzab = 0.f;
+          if (act) {
+            b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
             while (b * (b - 1) / 2 > pr) --b;
             while ((b + 1) * b / 2 <= pr) ++b;
-            const int a = pr - b * (b - 1) / 2;
-            const float eab = sm.pE[a] + sm.pE[b];
-            const float pzab = __fadd_rn(sm.pPz[a], sm.pPz[b]);
-            for (int c = 0; c < nneg; ++c) {
-              const bool e_ok = fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
-              cnt += e_ok;
-              cw += e_ok && !(prune && pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max));
-            }
+            a = pr - b * (b - 1) / 2;
+            eab = sm.pE[a] + sm.pE[b];
+            pzab = __fadd_rn(sm.pPz[a], sm.pPz[b]);
+          }
+          int cnt = 0, co = 0;
+          for (int c = 0; c < nneg; ++c) {
+            const bool e_ok = act && fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
+            const bool open = e_ok && !pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max);
+            cnt += e_ok;
+            co += open;
+            const bool wr = prune ? open : e_ok;
+            const unsigned m = __ballot_sync(FULL, wr);
+            const int k = nwrite + __popc(m & ((1u << lane) - 1u));
+            if (wr && k < S3_BUF) sm.wbuf[k] = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)c << 16);
+            nwrite += __popc(m);
           }
           ncombo += __reduce_add_sync(FULL, cnt);
-          nwrite += __reduce_add_sync(FULL, cw);
+          if (stats) nopen += __reduce_add_sync(FULL, co);
         }
+        __syncwarp();
         if (DEBUG && lane == 0) P.dump.n_combo[f] = ncombo;
         if (ncombo > C.max_combo) r = M3E_COMBO_OVERFLOW;
         else if (nwrite == 0) r = M3E_DROP;  // no combination, or none that can pass
@@ -301,33 +314,43 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
           for (int64_t t = cb + lane; t < S.combo_cap; t += 32) S.combo[t] = make_int4(-1, 0, 0, 0);
           r = DEFERRED;
         } else {
-          // pass 2: write them, in (pair, e-) order
-          long long w = cb;
-          for (int p0 = 0; p0 < npair; p0 += 32) {
-            const int pr = p0 + lane;
-            int a = 0, b = 0;
-            float eab = 0.f, pzab = 0.f;
-            const bool act = pr < npair;
-            if (act) {
-              b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
-              while (b * (b - 1) / 2 > pr) --b;
-              while ((b + 1) * b / 2 <= pr) ++b;
-              a = pr - b * (b - 1) / 2;
-              eab = sm.pE[a] + sm.pE[b];
-              pzab = __fadd_rn(sm.pPz[a], sm.pPz[b]);
+          if (nwrite <= S3_BUF) {
+            for (int t = lane; t < nwrite; t += 32) {
+              const uint32_t v = sm.wbuf[t];
+              S.combo[cb + t] = make_int4(f, sm.pidx[v & 255], sm.pidx[(v >> 8) & 255], sm.nidx[v >> 16]);
             }
-            for (int c = 0; c < nneg; ++c) {
-              const bool pass = act && fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win &&
-                                !(prune && pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max));
-              const unsigned m = __ballot_sync(FULL, pass);
-              if (pass) S.combo[w + __popc(m & ((1u << lane) - 1u))] = make_int4(f, sm.pidx[a], sm.pidx[b], sm.nidx[c]);
-              w += __popc(m);
+          } else {
+            // more than the buffer holds: a second pass writes them, in the same order
+            long long w = cb;
+            for (int p0 = 0; p0 < npair; p0 += 32) {
+              const int pr = p0 + lane;
+              int a = 0, b = 0;
+              float eab = 0.f, pzab = 0.f;
+              const bool act = pr < npair;
+              if (act) {
+                b = (int)((1.f + sqrtf(1.f + 8.f * (float)pr)) * 0.5f);
+                while (b * (b - 1) / 2 > pr) --b;
+                while ((b + 1) * b / 2 <= pr) ++b;
+                a = pr - b * (b - 1) / 2;
+                eab = sm.pE[a] + sm.pE[b];
+                pzab = __fadd_rn(sm.pPz[a], sm.pPz[b]);
+              }
+              for (int c = 0; c < nneg; ++c) {
+                const bool pass = act && fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win &&
+                                  !(prune && pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max));
+                const unsigned m = __ballot_sync(FULL, pass);
+                if (pass) S.combo[w + __popc(m & ((1u << lane) - 1u))] = make_int4(f, sm.pidx[a], sm.pidx[b], sm.nidx[c]);
+                w += __popc(m);
+              }
             }
           }
           if (lane == 0) {
             S.fcbase[f] = cb;
             S.fncombo[f] = nwrite;
-            if (stats) sm.acc[ST_COMBO] += ncombo;
+            if (stats) {
+              sm.acc[ST_COMBO] += ncombo;
+              sm.acc[ST_PZOPEN] += nopen;
+            }
           }
         }
       }
@@ -399,7 +422,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
   const int64_t n = min((int64_t)S.counters[1], S.combo_cap);
   const int64_t stride = (int64_t)gridDim.x * S4_WARPS * 32;
   int qn = 0;
-  unsigned nv = 0;
+  unsigned nv = 0, nvo = 0;
   for (int64_t base = ((int64_t)blockIdx.x * S4_WARPS + (threadIdx.x >> 5)) * 32;; base += stride) {
     const bool more = base < n;  // uniform in the warp
     if (more) {
@@ -439,6 +462,8 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
         const TrackR A = load_track(S.trec, r.y), B = load_track(S.trec, r.z), E = load_track(S.trec, r.w);
         const VtxOut v = vertex(A, B, E, C);
         nv += v.status == 2;
+        if (P.stats && v.status == 2)
+          nvo += !pz_fails_ptot(pz_sum(pz_track(A.p, A.ct), pz_track(B.p, B.ct), pz_track(E.p, E.ct)), C.ptot_max);
         if (v.pass) S.ffound[r.x] = 1;
         if (DEBUG) stage4_dump<DEBUG>(C, P, S, i, r, v, A.E + B.E + E.E);
       }
@@ -448,8 +473,9 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
     if (!more) break;
   }
   if (P.stats) {
-    const unsigned s = __reduce_add_sync(FULL, nv);
+    const unsigned s = __reduce_add_sync(FULL, nv), so = __reduce_add_sync(FULL, nvo);
     if (lane == 0 && s) atomicAdd(P.stats + ST_VTX, (unsigned long long)s);
+    if (lane == 0 && so) atomicAdd(P.stats + ST_VTXOPEN, (unsigned long long)so);
   }
 }
 

@@ -45,7 +45,7 @@ class Config(C.Structure):
 
 
 STATS_FIELDS = ("frames", "hits", "pair_tests", "triplet_tests", "triplets", "tracks", "energy_tests", "combos",
-                "vertexed", "deferred")
+                "vertexed", "deferred", "pz_open", "vertexed_pz_open")
 N_STATS = len(STATS_FIELDS) + 8
 
 

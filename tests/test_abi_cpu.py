@@ -102,3 +102,14 @@ def test_stream_entry_points_check_arguments(lib):
     assert L.m3e_stream_close(None) == m3e.EINVAL
     assert L.m3e_stream_open(None, None) == m3e.EINVAL
     assert L.m3e_stream_replay(None, None, None, 0, 1.0, 0, None, None, None, None, None) == m3e.EINVAL
+
+
+def test_stats_buffer_matches_the_c_layout(tmp_path):
+    """m3e_stats is read as an int64 buffer in STATS_FIELDS order, then reasons[8]."""
+    import shutil
+    if not shutil.which("gcc") or not os.path.exists("/usr/local/cuda/include/cuda_runtime.h"):
+        pytest.skip("gcc or the CUDA headers are missing")
+    from paper_2206_11535_gb300 import m3e
+    fields = list(m3e.STATS_FIELDS) + ["reasons"]
+    want = _c_layout("m3e_stats", fields, tmp_path)
+    assert want == [8 * m3e.N_STATS] + [8 * k for k in range(len(fields))]

@@ -229,8 +229,9 @@ def test_stats_counters(ctx, m3e, ocfg, form):
     ctx.select_frames_plain(*_dev(d), stats=stp)
     torch.cuda.synchronize()
     sp = m3e.stats_dict(stp)
-    for k in ("pair_tests", "triplet_tests", "triplets", "tracks", "energy_tests", "combos"):
+    for k in ("pair_tests", "triplet_tests", "triplets", "tracks", "energy_tests", "combos", "pz_open"):
         assert s[k] == sp[k], (k, s[k], sp[k])
+    assert 0 < s["pz_open"] < s["combos"] and s["vertexed_pz_open"] <= s["vertexed"]
     assert 0 < s["pair_tests"] <= cnt[:, 1].sum()
     # candidate triplets = sum over layer-1 hits of (Phi01 partners x Phi12 partners),
     # the oracle's count in FP64 (equal up to hits on a Phi-cut boundary)
