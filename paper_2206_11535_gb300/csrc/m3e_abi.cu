@@ -162,6 +162,7 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
     d.nlad[L] = c.n_ladders[L];
     d.nrow[L] = c.n_rows[L];
     d.ntot[L] = c.n_ladders[L] * c.n_cols[L];
+    d.intot[L] = (float)(1.0 / d.ntot[L]);
     const double x = c.x_over_X0[L];
     d.hl[L] = (float)(13.6 * std::sqrt(x) * (1.0 + 0.038 * std::log(x)));
     d.ihl[L] = (float)(1.0 / (13.6 * std::sqrt(x) * (1.0 + 0.038 * std::log(x))));

@@ -32,6 +32,7 @@ struct DevCfg {
   float rtc_lo2, rtc_hi2;     // (2 rtc_min)^2, (2 rtc_max)^2 against (d01 d12 d20)^2 / cross^2
   int k01, k12;               // phi-bin half windows of the two pair cuts
   int ntot[4], ncol[4], nlad[4], nrow[4];
+  float intot[4];             // 1 / ntot, rounded once (phi bin of a column, decode)
   int col_off[4], row_off[4]; // offsets of each layer in the look-up tables
   float kB;                   // p [MeV] = kB * R [mm]
   float hl[4];                // Highland width numerator: sigma_MS(p) = hl[layer] / p
