@@ -69,6 +69,7 @@ struct FrameSm {
   uint8_t p01[CH32 == 1 ? 1 : W_P01], p12[CH32 == 1 ? 1 : W_P12];
   uint16_t r01[CH32], r12[CH32];
   uint8_t c12[CH32];
+  uint8_t own[CH32 == 1 ? 1 : 32];  // warp stage, part C: layer-1 hit of each pair of a round
   int cst[CH32 + 1];
   TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
@@ -872,13 +873,22 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
         // are the same expressions as in the CTA stage.
         int nt = 0;
         const int T = basec;
-        int jc = 0;
+        int jc = 0;  // layer-1 hit of the first pair of the round
         for (int k0 = 0; k0 < T; k0 += 32) {
           const int k = k0 + lane;
-          int j = jc;
-          if (k < T)
-            while (sm.cst[j + 1] <= k) ++j;  // a chunk of pairs spans few layer-1 hits
-          jc = __shfl_sync(FULL, j, 31);
+          const int kend = min(k0 + 32, T);
+          // the owners of the round's pairs: lane t writes those of layer-1 hit jb + t
+          for (int jb = jc; jb < n1 && sm.cst[jb] < kend; jb += 32) {
+            const int jt = jb + lane;
+            if (jt < n1) {
+              const int e = min(sm.cst[jt + 1], kend);
+              for (int q = max(sm.cst[jt], k0); q < e; ++q) sm.own[q - k0] = (uint8_t)jt;
+            }
+          }
+          __syncwarp();
+          const int j = k < T ? sm.own[lane] : 0;
+          jc = sm.own[kend - 1 - k0];
+          __syncwarp();
           int i0 = 0, i1 = 0, r2 = 0, c2 = 0;
           float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f, tl01 = 0.f, zlo = 0.f, zhi = -1.f;
           if (k < T) {
