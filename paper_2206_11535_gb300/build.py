@@ -1,8 +1,10 @@
 """Build libm3e.so in-tree with nvcc for sm_103a (no torch extension machinery).
 
-Both translation units compile in parallel; the result is
-``paper_2206_11535_gb300/libm3e.so``.  Flags: IEEE division and square root,
-no flush-to-zero, no fast math.
+The translation units compile in parallel; the result is
+``paper_2206_11535_gb300/libm3e.so``.  Flags: the approximate (non-IEEE) FP32
+division and square root (CUDA's documented few-ulp forms, about 1e-7 relative,
+far inside the FP32-vs-FP64 tolerances of the parity tests), no flush-to-zero,
+no fast-math intrinsics for the transcendental functions.
 """
 from __future__ import annotations
 
@@ -18,7 +20,7 @@ OUT = os.path.join(HERE, "libm3e.so")
 UNITS = ["m3e_staged.cu", "m3e_fused.cu", "m3e_stream.cu", "m3e_grad.cu", "m3e_abi.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-         "--prec-div=true", "--prec-sqrt=true", "-ftz=false", "--fmad=true",
+         "--prec-div=false", "--prec-sqrt=false", "-ftz=false", "--fmad=true",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I" + os.path.join(ROOT, "include")]
 
 
