@@ -228,7 +228,8 @@ __device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx
   f.a0p = 0.5f * s1.dphi * dR;
   f.beta = s1.dth - s0.dth;
   f.b0p = (s1.th - s0.th) + s1.dth * dR;
-  const float sn = sinf(0.5f * (s0.th + s1.th));
+  // polar angles lie in (0, pi): the hardware sine (absolute error ~4e-7 on [-pi, pi])
+  const float sn = __sinf(0.5f * (s0.th + s1.th));
   f.s2 = sn * sn;
   const float den = f.alpha * f.alpha * f.s2 + f.beta * f.beta;
   const float u = -(f.alpha * f.a0p * f.s2 + f.beta * f.b0p) / den;
@@ -394,7 +395,7 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   // track for the vertex stage: transverse circle of radius R sin(theta01) through
   // the layer-0 and layer-1 hits, centre on the side the track turns to
   float st, ct;
-  sincosf(o.th01, &st, &ct);
+  __sincosf(o.th01, &st, &ct);  // theta01 in (0, pi), as in fit_triplet
   const float eps = kb > 0.f ? 1.f : -1.f;
   const float rt = Rb * st;
   const float dx = x1 - x0, dy = y1 - y0;
