@@ -57,20 +57,21 @@ struct TrkSoA {
 template <int CH, int CT, int CK, int CC, bool PHI = true, bool IDX = true, int CH32 = (CH <= W_HITS ? CH : 1)>
 struct FrameSm {
   static constexpr bool kPhi = PHI, kIdx = IDX;
+  static constexpr bool kPackB = CH < 256;  // bucket cursors as bytes, four to a word
   using TripT = typename std::conditional<(CH <= 256), uchar4, ushort4>::type;
   float x[CH], y[CH], z[CH], phi[PHI ? CH : 1];
   uint32_t addr[CH];
   uint16_t inidx[IDX ? CH : 1];
   uint8_t bin[CH];
   uint16_t bstart[NBK + 1];
-  int bcur[NBK];
+  uint32_t bcur[kPackB ? NBK / 4 : NBK];  // bucket counts, then cursors
   // warp stage, selection cuts: Phi01 / Phi12 partners of the layer-1 hits (regions
   // r01 / r12, counts c12) and the start of each layer-1 hit's candidate triplets
   uint8_t p01[CH32 == 1 ? 1 : W_P01], p12[CH32 == 1 ? 1 : W_P12];
   uint16_t r01[CH32], r12[CH32];
   uint8_t c12[CH32];
   uint8_t own[CH32 == 1 ? 1 : 32];  // warp stage, part C: layer-1 hit of each pair of a round
-  int cst[CH32 + 1];
+  uint16_t cst[CH32 + 1];
   TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
     TripT trip[CT];             // selected triplets (sorted-hit indices)
@@ -663,15 +664,32 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
 // ------------------------------------------------------------------ one frame
 
 
-template <class G>
-__device__ __forceinline__ void bucket_scan(const G& g, int* bcur, uint16_t* bstart) {
+// Add one hit to bucket key; returns the bucket's count (cursor) before it.  With
+// packed cursors a bucket is one byte of a word: counts and starts stay below the
+// 256 hits such a frame can hold, so no byte carries into the next.
+template <class S>
+__device__ __forceinline__ int bucket_add(S& sm, int key) {
+  if constexpr (S::kPackB) {
+    const int sh = 8 * (key & 3);
+    return (int)((atomicAdd(&sm.bcur[key >> 2], 1u << sh) >> sh) & 255u);
+  } else {
+    return (int)atomicAdd(&sm.bcur[key], 1u);
+  }
+}
+
+// Exclusive prefix of the bucket counts: bucket starts into bstart and, as the
+// placement cursors, back into bcur.
+template <class G, class S>
+__device__ __forceinline__ void bucket_scan(const G& g, S& sm) {
+  static_assert(NBK == 4 * 32, "one word of four packed buckets per lane");
   if (g.rank() < 32) {
     const int lane = g.rank();
     int v[NBK / 32];
     int s = 0;
 #pragma unroll
     for (int k = 0; k < NBK / 32; ++k) {
-      v[k] = bcur[lane * (NBK / 32) + k];
+      if constexpr (S::kPackB) v[k] = (int)((sm.bcur[lane] >> (8 * k)) & 255u);
+      else v[k] = (int)sm.bcur[lane * (NBK / 32) + k];
       s += v[k];
     }
     int inc = s;
@@ -681,13 +699,16 @@ __device__ __forceinline__ void bucket_scan(const G& g, int* bcur, uint16_t* bst
       if (lane >= o) inc += t;
     }
     int ex = inc - s;
+    uint32_t w = 0;
 #pragma unroll
     for (int k = 0; k < NBK / 32; ++k) {
-      bstart[lane * (NBK / 32) + k] = (uint16_t)ex;
-      bcur[lane * (NBK / 32) + k] = ex;
+      sm.bstart[lane * (NBK / 32) + k] = (uint16_t)ex;
+      if constexpr (S::kPackB) w |= (uint32_t)ex << (8 * k);
+      else sm.bcur[lane * (NBK / 32) + k] = (uint32_t)ex;
       ex += v[k];
     }
-    if (lane == 31) bstart[NBK] = (uint16_t)inc;
+    if constexpr (S::kPackB) sm.bcur[lane] = w;
+    if (lane == 31) sm.bstart[NBK] = (uint16_t)inc;
   }
   g.sync();
 }
@@ -718,7 +739,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
   const int32_t* hp = P.hits + base;
 
   // ---- A: decode and histogram
-  for (int k = g.rank(); k < NBK; k += G::N) sm.bcur[k] = 0;
+  for (int k = g.rank(); k < (S::kPackB ? NBK / 4 : NBK); k += G::N) sm.bcur[k] = 0;
   if (g.leader()) {
     sm.bad = 0;
     sm.ntrip = 0;
@@ -734,7 +755,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
   for (int i = g.rank(); i < n; i += G::N) {
     const Dec d = decode(C, (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i)));
     if (!d.ok) sm.bad = 1;
-    else if (n <= CH) atomicAdd(&sm.bcur[d.L * NB + d.b], 1);
+    else if (n <= CH) bucket_add(sm, d.L * NB + d.b);
   }
   g.sync();
   if (sm.bad) {
@@ -748,12 +769,12 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
   }
 
   // ---- B: counting sort by (layer, phi bin)
-  bucket_scan(g, sm.bcur, sm.bstart);
+  bucket_scan(g, sm);
   for (int i = g.rank(); i < n; i += G::N) {
     const uint32_t a = (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i));
     const Dec d = decode(C, a);
     const int key = d.L * NB + d.b;
-    const int pos = atomicAdd(&sm.bcur[key], 1);
+    const int pos = bucket_add(sm, key);
     const float4 cl = __ldg(P.col_lut + C.col_off[d.L] + d.g);
     sm.x[pos] = cl.x;
     sm.y[pos] = cl.y;
@@ -858,10 +879,10 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           const int t = __shfl_up_sync(FULL, ec, o);
           if (lane >= o) ec += t;
         }
-        if (j < n1) sm.cst[j] = basec + ec - pc;
+        if (j < n1) sm.cst[j] = (uint16_t)(basec + ec - pc);
         basec += __shfl_sync(FULL, ec, 31);
       }
-      if (lane == 0) sm.cst[n1] = basec;
+      if (lane == 0) sm.cst[n1] = (uint16_t)basec;
       sm.bad = __any_sync(FULL, over) ? 2 : 0;
       __syncwarp();
       if (sm.bad == 2) {

@@ -17,7 +17,7 @@ namespace m3e {
 namespace {
 
 constexpr int NL3 = NB + 1;                        // layer-3 bin starts per frame
-constexpr int S1_TRIP = 256;                       // stage-1 warp-tier triplet capacity
+constexpr int S1_TRIP = 160;                       // stage-1 warp-tier triplet capacity
 using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1, false, false>;  // phi re-read at emit, no input indices
 using SmFrontD = FrameSm<W_HITS, S1_TRIP, 1, 1>;                // candidate record: with input indices
 constexpr int M_HITS = 1024;                       // stage-1 middle tier (CTA per frame)
