@@ -168,11 +168,25 @@ int m3e_select_frames_debug(m3e_ctx* ctx, int form, const int32_t* d_hits, const
                             int64_t n_frames, uint8_t* d_keep, uint8_t* d_reason, const m3e_dump* dump,
                             cudaStream_t stream);
 
-/* End to end from HOST memory: copies the hits and offsets to the device in
- * chunks, selects, and copies keep/reason back, overlapping the copies of one
- * chunk with the kernels of another on two internal streams.  Returns after
+/* End to end from HOST memory: copies the offsets and then the hits to the
+ * device in chunks of frames on an internal copy stream, while one staged
+ * selection over the whole batch runs on an internal compute stream, and copies
+ * keep/reason back.  After each chunk the copy engine writes that chunk's arrival
+ * flag; stage 1 takes a frame only once its chunk's flag is set, so it starts on
+ * the first chunk while the later ones are still on their way.  A wait for a
+ * chunk is bounded (m3e_set_host_pipeline); when it runs out the call's results
+ * are undefined and M3E_ETIMEOUT is latched (m3e_check).  Returns after
  * enqueueing; the results are in h_keep/h_reason once `stream` has reached the
- * call (the caller's stream waits for both internal streams). */
+ * call (the caller's stream waits for both internal streams).  Host buffers that
+ * are page-locked copy at full speed; others work, more slowly.  Consecutive calls
+ * on one context must be ordered by the caller's stream. */
+/* Settings of m3e_select_frames_host: at most max_chunks chunks (1..64, default
+ * 16; a chunk holds at least 50,000 frames unless the batch is smaller), a wait of
+ * at most wait_ms (1..60,000, default 2,000) for one chunk, and drop_chunk: -1 in
+ * normal use; k >= 0 leaves chunk k's flag unset, so that stage 1 runs out of its
+ * wait (a test of the bounded wait; the call then latches M3E_ETIMEOUT). */
+int m3e_set_host_pipeline(m3e_ctx* ctx, int max_chunks, int wait_ms, int drop_chunk);
+
 int m3e_select_frames_host(m3e_ctx* ctx, const int32_t* h_hits, const int64_t* h_frame_off, int64_t n_frames,
                            uint8_t* h_keep, uint8_t* h_reason, cudaStream_t stream);
 

@@ -48,8 +48,8 @@ struct DeviceGuard {
 // Chunks of the host entry point (double-buffered): at most 4, of at least 200,000
 // frames, so that the copy of the next chunk hides behind the kernels of this one
 // while the fixed cost per chunk (launches, kernel tails) stays small.
-constexpr int HOST_CHUNKS = 4;
-constexpr int64_t HOST_CHUNK_MIN_FRAMES = 200000;
+constexpr int GATE_MAX = 64;                  // chunks of the host entry point, at most
+constexpr int64_t GATE_MIN_FRAMES = 50000;    // frames per chunk, at least (unless the batch is smaller)
 
 }  // namespace
 
@@ -109,6 +109,10 @@ struct m3e_ctx {
   int64_t* d_off[2] = {nullptr, nullptr};
   uint8_t* d_out[2] = {nullptr, nullptr};
   int64_t cap_hits[2] = {0, 0}, cap_frames[2] = {0, 0};
+  unsigned* d_gate = nullptr;   // per-chunk arrival flags
+  unsigned* h_gate = nullptr;   // pinned constants the copy engine writes into them: GATE_MAX zeros, then a one
+  cudaEvent_t ge[2] = {nullptr, nullptr};  // flags cleared; every copy of the call done
+  int gate_chunks = 16, gate_ms = 2000, gate_drop = -1;
   // kernel timing
   bool prof = false;
   bool prof_valid = false;
@@ -360,7 +364,8 @@ enum { FORM_STAGED = 0, FORM_FUSED = 1, FORM_PLAIN = 2 };
 // Enqueue one batch on stream s: form 0 staged (5 kernels), 1 fused warp kernel,
 // 2 plain CTA-per-frame kernel; forms 0 and 1 finish with the deferred-frame
 // kernel.  Timing events are recorded when `timed`.
-int enqueue(m3e_ctx* x, Scratch& sc, KParams p, int form, bool debug, cudaStream_t s, bool timed) {
+int enqueue(m3e_ctx* x, Scratch& sc, KParams p, int form, bool debug, cudaStream_t s, bool timed,
+            cudaEvent_t after_s1 = nullptr) {
   if (form == FORM_PLAIN) {
     if (timed) CUDA_TRY(cudaEventRecord(x->pe[0], s));
     CUDA_TRY(launch_plain(x->dc, p, debug, s));
@@ -382,7 +387,8 @@ int enqueue(m3e_ctx* x, Scratch& sc, KParams p, int form, bool debug, cudaStream
   const int grids[6] = {x->sms * x->s1_bpsm, x->sms * x->s2_bpsm,  x->sms * x->s3_bpsm,
                         x->sms * x->s4_bpsm, x->sms * x->s1c_bpsm, x->sms * x->s1m_bpsm};
   const SParams sp = staged_params(sc);
-  CUDA_TRY(launch_staged(x->dc, p, sp, grids, debug, s, timed ? x->pe : nullptr));
+  if (p.gate) CUDA_TRY(cudaMemsetAsync(sp.fstate, 0x7f, sizeof(int) * (size_t)p.n_frames, s));  // no stale states
+  CUDA_TRY(launch_staged(x->dc, p, sp, grids, debug, s, timed ? x->pe : nullptr, after_s1));
   KParams pd = p;  // frames no stage could finish: the CTA-per-frame kernel
   pd.in_list = sp.list2;
   pd.in_count = sp.lcount + 1;
@@ -482,7 +488,10 @@ int m3e_destroy(m3e_ctx* x) {
     cudaFree(x->d_out[i]);
     if (x->hs[i]) cudaStreamDestroy(x->hs[i]);
     if (x->he[i]) cudaEventDestroy(x->he[i]);
+    if (x->ge[i]) cudaEventDestroy(x->ge[i]);
   }
+  cudaFree(x->d_gate);
+  if (x->h_gate) cudaFreeHost(x->h_gate);
   for (int i = 0; i < 10; ++i)
     if (x->pe[i]) cudaEventDestroy(x->pe[i]);
   delete x;
@@ -598,14 +607,19 @@ int m3e_check(m3e_ctx* x, cudaStream_t s) {
   if (e) {
     CUDA_TRY(cudaMemsetAsync(x->err, 0, sizeof(int), s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    if (e & ERR_GATE) return fail(M3E_ETIMEOUT, "a chunk of the host entry point did not arrive in time");
     return fail(M3E_EBADHIT, "invalid pixel address or frame size seen (flags %d)", e);
   }
   return M3E_OK;
 }
 
-// End to end from host memory.  Frames are cut into chunks of about equal hit
-// count; chunk k uses buffer set k % 2 and internal stream k % 2, so the copies
-// of one chunk overlap the kernels of the other.  Each chunk runs the staged form.
+// End to end from host memory.  One staged selection over the whole batch on
+// internal stream 0, while internal stream 1 copies the offsets and then the hits
+// in chunks of frames, each followed by a 4-byte copy that sets the chunk's arrival
+// flag.  Stage 1 takes a frame only once its chunk has arrived (a bounded wait), so
+// the selection starts after the first chunk instead of after the whole batch; the
+// kernels after stage 1 wait for the last copy.  The flags are cleared and set by
+// the copy engine from constant page-locked words, so no host write races them.
 int m3e_select_frames_host(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_off, int64_t n, uint8_t* h_keep,
                            uint8_t* h_reason, cudaStream_t s) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
@@ -625,61 +639,86 @@ int m3e_select_frames_host(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_o
   CUDA_TRY(cudaEventRecord(x->he[0], s));
   for (int i = 0; i < 2; ++i) CUDA_TRY(cudaStreamWaitEvent(x->hs[i], x->he[0], 0));
   const int64_t total = h_off[n] - h_off[0];
-  const int64_t by_size = n / HOST_CHUNK_MIN_FRAMES;
-  const int nch = (int)(by_size < 1 ? 1 : (by_size > HOST_CHUNKS ? HOST_CHUNKS : by_size));
-  int64_t f0 = 0;
-  int launches = 0;
-  for (int k = 0; k < nch; ++k) {
-    int64_t f1 = n;
-    if (k + 1 < nch) {  // chunk end: first frame whose start reaches (k+1)/nch of the hits
-      const int64_t target = h_off[0] + total * (k + 1) / nch;
-      int64_t lo = f0 + 1, hi = n - (nch - k - 1);
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) / 2;
-        if (h_off[mid] >= target) hi = mid; else lo = mid + 1;
-      }
-      f1 = lo;
-    }
-    const int b = k & 1;
-    const int64_t nf = f1 - f0, nh = h_off[f1] - h_off[f0];
-    cudaStream_t hs = x->hs[b];
-    rc = grow(x->d_hits[b], x->cap_hits[b], nh + nh / 4 + 1024, sizeof(int32_t), "staging hits");
-    if (rc) return rc;
-    if (nf + 1 > x->cap_frames[b]) {
-      cudaFree(x->d_off[b]);
-      cudaFree(x->d_out[b]);
-      x->d_off[b] = nullptr;
-      x->d_out[b] = nullptr;
-      x->cap_frames[b] = 0;
-      const int64_t cap = nf + nf / 4 + 1024;
-      if (cudaMalloc(&x->d_off[b], sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
-          cudaMalloc(&x->d_out[b], 2 * cap) != cudaSuccess)
-        return fail(M3E_ENOMEM, "staging frames");
-      x->cap_frames[b] = cap;
-    }
-    rc = ensure_scratch(x->hsc[b], nf, true);
-    if (rc) return rc;
-    CUDA_TRY(cudaMemcpyAsync(x->d_hits[b], h_hits + h_off[f0], sizeof(int32_t) * nh, cudaMemcpyHostToDevice, hs));
-    CUDA_TRY(cudaMemcpyAsync(x->d_off[b], h_off + f0, sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice, hs));
-    KParams p = base_params(x, x->hsc[b]);
-    p.hits = x->d_hits[b];
-    p.off = x->d_off[b];
-    p.off_base = h_off[f0];
-    p.n_frames = nf;
-    p.keep = x->d_out[b];
-    p.reason = x->d_out[b] + x->cap_frames[b];
-    rc = enqueue(x, x->hsc[b], p, FORM_STAGED, false, hs, false);
-    if (rc) return rc;
-    launches += x->last_launches;
-    CUDA_TRY(cudaMemcpyAsync(h_keep + f0, p.keep, nf, cudaMemcpyDeviceToHost, hs));
-    CUDA_TRY(cudaMemcpyAsync(h_reason + f0, p.reason, nf, cudaMemcpyDeviceToHost, hs));
-    f0 = f1;
+  if (!x->d_gate) {
+    if (cudaMalloc(&x->d_gate, sizeof(unsigned) * GATE_MAX) != cudaSuccess) return fail(M3E_ENOMEM, "chunk flags");
   }
+  if (!x->h_gate) {
+    if (cudaMallocHost(&x->h_gate, sizeof(unsigned) * (GATE_MAX + 1)) != cudaSuccess)
+      return fail(M3E_ENOMEM, "chunk flag constants");
+    for (int k = 0; k < GATE_MAX; ++k) x->h_gate[k] = 0u;
+    x->h_gate[GATE_MAX] = 1u;
+  }
+  for (int i = 0; i < 2; ++i)
+    if (!x->ge[i]) CUDA_TRY(cudaEventCreateWithFlags(&x->ge[i], cudaEventDisableTiming));
+  rc = grow(x->d_hits[0], x->cap_hits[0], total + total / 4 + 1024, sizeof(int32_t), "staging hits");
+  if (rc) return rc;
+  if (n + 1 > x->cap_frames[0]) {
+    cudaFree(x->d_off[0]);
+    cudaFree(x->d_out[0]);
+    x->d_off[0] = nullptr;
+    x->d_out[0] = nullptr;
+    x->cap_frames[0] = 0;
+    const int64_t cap = n + n / 4 + 1024;
+    if (cudaMalloc(&x->d_off[0], sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
+        cudaMalloc(&x->d_out[0], 2 * cap) != cudaSuccess)
+      return fail(M3E_ENOMEM, "staging frames");
+    x->cap_frames[0] = cap;
+  }
+  rc = ensure_scratch(x->hsc[0], n, true);
+  if (rc) return rc;
+  // chunks of about equal frame counts
+  const int64_t by_size = n / GATE_MIN_FRAMES;
+  const int nch = (int)(by_size < 1 ? 1 : (by_size > x->gate_chunks ? x->gate_chunks : by_size));
+  const int64_t fpc = (n + nch - 1) / nch;
+  cudaStream_t ps = x->hs[0], cs = x->hs[1];
+  // copy stream: clear the flags, then the offsets, then each chunk's hits and its flag
+  CUDA_TRY(cudaMemcpyAsync(x->d_gate, x->h_gate, sizeof(unsigned) * nch, cudaMemcpyHostToDevice, cs));
+  CUDA_TRY(cudaEventRecord(x->ge[0], cs));
+  CUDA_TRY(cudaMemcpyAsync(x->d_off[0], h_off, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, cs));
+  for (int k = 0; k < nch; ++k) {
+    const int64_t f0 = k * fpc, f1 = f0 + fpc < n ? f0 + fpc : n;
+    const int64_t nh = f0 < n ? h_off[f1] - h_off[f0] : 0;
+    if (nh > 0)
+      CUDA_TRY(cudaMemcpyAsync(x->d_hits[0] + (h_off[f0] - h_off[0]), h_hits + h_off[f0], sizeof(int32_t) * nh,
+                               cudaMemcpyHostToDevice, cs));
+    if (k != x->gate_drop)
+      CUDA_TRY(cudaMemcpyAsync(x->d_gate + k, x->h_gate + GATE_MAX, sizeof(unsigned), cudaMemcpyHostToDevice, cs));
+  }
+  CUDA_TRY(cudaEventRecord(x->ge[1], cs));
+  // compute stream: starts once the flags are clear; the kernels after stage 1
+  // also wait for the last copy
+  CUDA_TRY(cudaStreamWaitEvent(ps, x->ge[0], 0));
+  KParams p = base_params(x, x->hsc[0]);
+  p.hits = x->d_hits[0];
+  p.off = x->d_off[0];
+  p.off_base = h_off[0];
+  p.n_frames = n;
+  p.keep = x->d_out[0];
+  p.reason = x->d_out[0] + x->cap_frames[0];
+  p.gate = x->d_gate;
+  p.gate_frames = (int)fpc;
+  p.gate_ms = x->gate_ms;
+  rc = enqueue(x, x->hsc[0], p, FORM_STAGED, false, ps, false, x->ge[1]);
+  if (rc) return rc;
+  const int launches = x->last_launches;
+  CUDA_TRY(cudaMemcpyAsync(h_keep, p.keep, n, cudaMemcpyDeviceToHost, ps));
+  CUDA_TRY(cudaMemcpyAsync(h_reason, p.reason, n, cudaMemcpyDeviceToHost, ps));
   for (int i = 0; i < 2; ++i) {
     CUDA_TRY(cudaEventRecord(x->he[i], x->hs[i]));
     CUDA_TRY(cudaStreamWaitEvent(s, x->he[i], 0));
   }
   x->last_launches = launches;
+  return M3E_OK;
+}
+
+int m3e_set_host_pipeline(m3e_ctx* x, int max_chunks, int wait_ms, int drop_chunk) {
+  if (!x) return fail(M3E_EINVAL, "ctx is NULL");
+  if (max_chunks < 1 || max_chunks > GATE_MAX) return fail(M3E_EINVAL, "max_chunks 1..%d", GATE_MAX);
+  if (wait_ms < 1 || wait_ms > 60000) return fail(M3E_EINVAL, "wait_ms 1..60000");
+  if (drop_chunk < -1) return fail(M3E_EINVAL, "drop_chunk >= -1");
+  x->gate_chunks = max_chunks;
+  x->gate_ms = wait_ms;
+  x->gate_drop = drop_chunk;
   return M3E_OK;
 }
 

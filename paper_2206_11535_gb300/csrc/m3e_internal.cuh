@@ -65,6 +65,9 @@ struct KParams {
   const int* in_count;        // ... and their number
   int grab;                   // frames per work-queue grab
   int defer_hits;             // warp stages defer frames with more hits (<= W_HITS)
+  const unsigned* gate;       // host entry point: per-chunk arrival flags (written by the copy engine), or null
+  int gate_frames;            // frames per chunk
+  int gate_ms;                // longest wait for one chunk
   m3e_dump dump;              // all pointers null unless debugging
 };
 
@@ -93,14 +96,14 @@ struct SParams {
 enum { ST_FRAMES = 0, ST_HITS, ST_PAIRS, ST_TTESTS, ST_TRIP, ST_TRK, ST_ETEST, ST_COMBO, ST_VTX, ST_DEFER,
        ST_PZOPEN, ST_VTXOPEN, ST_REASON0 };
 
-enum { ERR_BADHIT = 1, ERR_NEGSIZE = 2 };
+enum { ERR_BADHIT = 1, ERR_NEGSIZE = 2, ERR_GATE = 4 };
 
 // Host-side launchers (m3e_fused.cu, m3e_staged.cu).
 cudaError_t launch_fused(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
 cudaError_t launch_deferred(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
 cudaError_t launch_plain(const DevCfg& c, const KParams& p, bool debug, cudaStream_t s);
 cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
-                          cudaStream_t st, cudaEvent_t* ev);
+                          cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1 = nullptr);
 size_t stage1c_smem_bytes();
 int fused_blocks_per_sm();
 int stage_blocks_per_sm(int stage);

@@ -120,8 +120,44 @@ __device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const DevCfg& 
   g.sync();
 }
 
-// ---- stage 1, warp tier: one warp per frame, frames from the device queue
-template <bool DEBUG>
+__device__ __forceinline__ unsigned ld_acquire_sys_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Host entry point: wait until the copy engine has flagged chunk k as arrived.
+// The wait is bounded by P.gate_ms; it also ends once another warp has given up.
+// Returns false when it gave up (ERR_GATE latched).
+__device__ bool gate_wait(const KParams& P, int k) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long t_end = global_ns() + (unsigned long long)P.gate_ms * 1000000ull;
+    unsigned ns = 64;
+    while (ld_acquire_sys_u32(P.gate + k) == 0u) {
+      if ((*(volatile int*)P.err & ERR_GATE) || global_ns() > t_end) {
+        atomicOr(P.err, ERR_GATE);
+        ok = 0;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 2048) ns *= 2;
+    }
+  }
+  __syncwarp();
+  return __shfl_sync(FULL, ok, 0) != 0;
+}
+
+// ---- stage 1, warp tier: one warp per frame, frames from the device queue.
+// GATED (host entry point): the hits arrive while the kernel runs; a frame is
+// taken only after its chunk's arrival flag, and the hits are read past L1.
+template <bool DEBUG, bool GATED = false>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     k_stage1(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,14 +167,26 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
   const WarpGroup g;
   clear_stats(g, sm);
   const int nf = (int)P.n_frames;
-  for (;;) {
+  int arrived = -1;  // chunks up to this one are known to have arrived
+  bool stop = false;
+  while (!stop) {
     int f0 = 0;
     if (g.leader()) f0 = atomicAdd(&P.work[0], P.grab);
     f0 = __shfl_sync(FULL, f0, 0);
     if (f0 >= nf) break;
     const int f1 = min(f0 + P.grab, nf);
     for (int f = f0; f < f1; ++f) {
-      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG>(g, sm, C, P, f);
+      if constexpr (GATED) {
+        const int k = f / P.gate_frames;
+        if (k > arrived) {
+          if (!gate_wait(P, k)) {
+            stop = true;
+            break;
+          }
+          arrived = k;
+        }
+      }
+      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED>(g, sm, C, P, f);
       stage1_finish<WarpGroup, Sm, DEBUG>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
     }
   }
@@ -538,9 +586,11 @@ int stage_blocks_per_sm(int stage) {
 // stage 3 end up in S.list2 for the caller's CTA-per-frame kernel.  ev (9 events or
 // null): before stage 1 and after each kernel.
 cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
-                          cudaStream_t st, cudaEvent_t* ev) {
+                          cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1) {
   const size_t sm1 = stage1_smem_bytes(debug), smc = stage1c_smem_bytes(), smm = stage1m_smem_bytes();
-  cudaError_t e = debug ? set_smem(k_stage1<true>, sm1) : set_smem(k_stage1<false>, sm1);
+  const bool gated = p.gate != nullptr && !debug;
+  cudaError_t e = debug ? set_smem(k_stage1<true>, sm1)
+                        : (gated ? set_smem(k_stage1<false, true>, sm1) : set_smem(k_stage1<false>, sm1));
   if (e == cudaSuccess)
     e = debug ? set_smem(k_stage1c<SmFrontCta, C_HITS, true>, smc) : set_smem(k_stage1c<SmFrontCta, C_HITS, false>, smc);
   if (e == cudaSuccess)
@@ -561,7 +611,10 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   p3.defer_count = s.lcount + 1;
   if (ev) cudaEventRecord(ev[0], st);
   if (debug) k_stage1<true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
+  else if (gated) k_stage1<false, true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   else k_stage1<false><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
+  // the later kernels read the hits too: order them after every copy of the host entry
+  if (after_s1) cudaStreamWaitEvent(st, after_s1, 0);
   if (ev) cudaEventRecord(ev[1], st);
   if (debug) k_stage1c<SmFrontMid, M_HITS, true><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
   else k_stage1c<SmFrontMid, M_HITS, false><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);

@@ -105,6 +105,7 @@ def _load(path: str = LIB_PATH):
     lib.m3e_select_frames_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.m3e_check.argtypes = [vp, vp]
     lib.m3e_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    lib.m3e_set_host_pipeline.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.m3e_last_launch_count.argtypes = [vp]
     lib.m3e_last_error_string.restype = C.c_char_p
     lib.m3e_set_profiling.argtypes = [vp, C.c_int]
@@ -266,6 +267,12 @@ class Context:
         _check(lib.m3e_select_frames_noalloc(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
                                              _stream(stream)))
         return keep, reason
+
+    def set_host_pipeline(self, max_chunks: int = 16, wait_ms: int = 2000, drop_chunk: int = -1):
+        """``m3e_set_host_pipeline``: chunking and the bounded chunk wait of
+        select_frames_host (drop_chunk >= 0 leaves that chunk's arrival flag unset:
+        a test of the wait)."""
+        _check(lib.m3e_set_host_pipeline(self._h, max_chunks, wait_ms, drop_chunk))
 
     def select_frames_host(self, hits: np.ndarray, off: np.ndarray, keep=None, reason=None, stream=None):
         """``m3e_select_frames_host`` on host arrays (numpy or pinned torch CPU tensors).

@@ -192,20 +192,55 @@ def test_small_caps_overflow_parity(m3e, cfg):
             assert counts[2] > 0 and counts[3] > 0 and counts[4] > 0, counts
 
 
-def test_host_entry_matches_device(ctx):
-    """The host entry point (copies overlapped with the kernels, four chunks at this
-    size) decides as the device entry point."""
+def test_host_entry_matches_device(ctx, m3e):
+    """The host entry point (the selection running while the chunks of the batch
+    arrive; 16 chunks at this size) decides as the device entry point, from
+    page-locked and from ordinary host memory, call after call, and for a batch
+    that fits one chunk."""
     d = gen.workload("c1", n_frames=850_000, seed=12)
     keep, reason = ctx.select_frames(*_dev(d))
+    reason, keep = reason.cpu().numpy(), keep.cpu().numpy()
     hh = torch.from_numpy(d["hits"]).pin_memory()
     ho = torch.from_numpy(d["off"]).pin_memory()
     hk = torch.empty(d["off"].size - 1, dtype=torch.uint8).pin_memory()
     hr = torch.empty(d["off"].size - 1, dtype=torch.uint8).pin_memory()
     s = torch.cuda.current_stream()
-    ctx.select_frames_host(hh, ho, hk, hr, stream=s)
+    for _ in range(3):
+        hr.fill_(9)
+        ctx.select_frames_host(hh, ho, hk, hr, stream=s)
+        s.synchronize()
+        assert (hr.numpy() == reason).all()
+        assert (hk.numpy() == keep).all()
+    ctx.check()
+    k2, r2 = ctx.select_frames_host(d["hits"], d["off"], stream=s)
     s.synchronize()
-    assert (hr.numpy() == reason.cpu().numpy()).all()
-    assert (hk.numpy() == keep.cpu().numpy()).all()
+    assert (r2 == reason).all() and (k2 == keep).all()
+    n = 20_000  # one chunk
+    k3, r3 = ctx.select_frames_host(d["hits"][:d["off"][n]], d["off"][:n + 1], stream=s)
+    s.synchronize()
+    assert (r3 == reason[:n]).all()
+    ctx.check()
+
+
+def test_host_entry_chunk_wait_is_bounded(cfg, m3e):
+    """A chunk whose arrival flag is never set: stage 1 gives up after the wait
+    limit, the call latches ETIMEOUT, and the context stays usable."""
+    d = gen.workload("c1", n_frames=300_000, seed=14)
+    with m3e.Context(cfg, 0) as c:
+        ref = c.select_frames(*_dev(d))[1].cpu().numpy()
+        s = torch.cuda.current_stream()
+        c.set_host_pipeline(max_chunks=6, wait_ms=50, drop_chunk=3)
+        c.select_frames_host(d["hits"], d["off"], stream=s)
+        with pytest.raises(m3e.M3EError) as e:
+            c.check(stream=s)
+        assert e.value.code == m3e.ETIMEOUT
+        c.set_host_pipeline()
+        _, r = c.select_frames_host(d["hits"], d["off"], stream=s)
+        s.synchronize()
+        assert (r == ref).all()
+        c.check(stream=s)
+        with pytest.raises(m3e.M3EError):
+            c.set_host_pipeline(max_chunks=0)
 
 
 @pytest.mark.parametrize("form", ["staged", "fused"])
