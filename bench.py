@@ -149,10 +149,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(n_frames: int, stage: str):
-    """DRAM bytes (read + write) of one batch's launches of the given stage, from the committed
-    ncu summary (bytes per frame of a smaller batch of the same workload, scaled to n_frames);
-    None when the summary was taken on other kernel sources."""
+def _recorded(key: str):
+    """A per-frame counter of the committed ncu summary of the stage kernels, or None
+    when the summary was taken on other kernel sources (or lacks the key)."""
     p = os.path.join(ROOT, "profiles", "staged_c2_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -164,9 +163,17 @@ def recorded_traffic(n_frames: int, stage: str):
     if kv.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_frame." + stage]) * n_frames
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
+
+
+def recorded_traffic(n_frames: int, stage: str):
+    """DRAM bytes (read + write) of one batch's launches of the given stage, from the committed
+    ncu summary (bytes per frame of a smaller batch of the same workload, scaled to n_frames);
+    None when the summary was taken on other kernel sources."""
+    v = _recorded("dram_bytes_per_frame." + stage)
+    return None if v is None else v * n_frames
 
 
 def cpu_baseline(d, seconds_target=12.0):
@@ -537,6 +544,15 @@ def main():
                            f"{f_mhz:.0f} MHz (median sampled under load)",
             "stages": stages,
             "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf}
+    # the same kernel's use of its issue slots: warp instructions per frame from the ncu
+    # capture, over this run's kernel time, against 4 schedulers x SMs x clock
+    wi = _recorded("warp_inst_per_frame." + dom["kernel"].split()[0])
+    ia = _recorded("issue_active_pct." + dom["kernel"].split()[0])
+    if wi is not None and dom["ms"] > 0:
+        ipk = 4 * props.multi_processor_count * f_mhz * 1e6
+        ach = wi * nf / (dom["ms"] / 1e3)
+        roof["issue"] = {"achieved": ach, "peak": ipk, "unit": "warp instructions/s", "frac": ach / ipk,
+                         "warp_instructions_per_frame": wi, "ncu_issue_active_pct": ia}
     # muon-rate sweep
     rates = None
     if "rates" in arms and world == 1:
