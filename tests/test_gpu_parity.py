@@ -222,6 +222,52 @@ def test_host_entry_matches_device(ctx, m3e):
     ctx.check()
 
 
+def test_host_entry_edge_cases(ctx, m3e, cfg):
+    """The host entry point on ragged batches: runs of empty frames across chunk
+    boundaries, a batch without a single hit, one frame, an invalid address (kept,
+    EBADHIT latched), and the edge frames of the device test."""
+    g = cfg["geometry"]
+    s = torch.cuda.current_stream()
+    d = gen.workload("c1", n_frames=120_000, seed=15)
+    sizes = np.diff(d["off"])
+    sizes[40_000:70_000] = 0  # empty frames, across the boundaries of 50,000-frame chunks
+    hits = np.concatenate([d["hits"][d["off"][f]:d["off"][f + 1]] for f in range(sizes.size) if sizes[f]])
+    off = np.zeros(sizes.size + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    assert off[-1] == hits.size
+    dd = dict(hits=hits.astype(np.int32), off=off)
+    ref = ctx.select_frames(*_dev(dd))[1].cpu().numpy()
+    ctx.set_host_pipeline(max_chunks=3)
+    try:
+        _, r = ctx.select_frames_host(dd["hits"], dd["off"], stream=s)
+        s.synchronize()
+        assert (r == ref).all()
+        ctx.check()
+    finally:
+        ctx.set_host_pipeline()
+    # no hits at all, and a single frame
+    z = dict(hits=np.zeros(0, np.int32), off=np.zeros(7, np.int64))
+    _, r = ctx.select_frames_host(z["hits"], z["off"], stream=s)
+    s.synchronize()
+    assert (r == ctx.select_frames(*_dev(z))[1].cpu().numpy()).all()
+    one = dict(hits=d["hits"][:d["off"][1]].copy(), off=d["off"][:2].copy())
+    _, r = ctx.select_frames_host(one["hits"], one["off"], stream=s)
+    s.synchronize()
+    assert r[0] == ref[0]
+    # an invalid address in the second frame
+    f0 = d["hits"][:d["off"][1]]
+    bad = np.concatenate([f0, gen.encode([2], [g["n_ladders"][2]], [0], [0])]).astype(np.int32)
+    hb = np.concatenate([f0, bad]).astype(np.int32)
+    ob = np.array([0, f0.size, f0.size + bad.size], np.int64)
+    k, r = ctx.select_frames_host(hb, ob, stream=s)
+    s.synchronize()
+    assert r[1] == m3e.ERR_BADHIT and k[1] == 1 and r[0] == ref[0]
+    with pytest.raises(m3e.M3EError) as e:
+        ctx.check(stream=s)
+    assert e.value.code == m3e.EBADHIT
+    ctx.check(stream=s)
+
+
 def test_host_entry_chunk_wait_is_bounded(cfg, m3e):
     """A chunk whose arrival flag is never set: stage 1 gives up after the wait
     limit, the call latches ETIMEOUT, and the context stays usable."""
