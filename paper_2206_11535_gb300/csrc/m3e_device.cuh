@@ -1,6 +1,8 @@
 // Device code shared by the fused and the staged selection kernels: thread
 // groups, the shared-memory frame stage, decode, the triplet fit, track
-// reconstruction and the vertex, all in FP32 with IEEE division and square root.
+// reconstruction and the vertex, all in FP32 (the build uses the approximate
+// division and square root, a few ulp; exact comparisons that decide an integer
+// use explicitly rounded intrinsics).
 #pragma once
 
 #include <cfloat>
