@@ -61,16 +61,20 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, 
     for (int64_t t = tb + g.rank(); t < S.trip_cap && t < tb + ntrip; t += G::N) S.trip[t] = make_int4(-1, 0, 0, 0);
     return false;
   }
+  // phi and the address of a sorted hit serve only the layer-3 search of stage 2
+  const int l3s = sm.bstart[3 * NB];
   for (int i = g.rank(); i < n; i += G::N) {
-    float phi;
-    if constexpr (Sm::kPhi) {
-      phi = sm.phi[i];
-    } else {
-      const Dec d = decode(C, sm.addr[i]);
-      phi = __ldg(P.col_lut + C.col_off[d.L] + d.g).z;
+    float phi = 0.f;
+    if (i >= l3s) {
+      if constexpr (Sm::kPhi) {
+        phi = sm.phi[i];
+      } else {
+        const Dec d = decode(C, sm.addr[i]);
+        phi = __ldg(P.col_lut + C.col_off[d.L] + d.g).z;
+      }
+      S.haddr[hb + i] = sm.addr[i];
     }
     S.hp[hb + i] = make_float4(sm.x[i], sm.y[i], sm.z[i], phi);
-    S.haddr[hb + i] = sm.addr[i];
     if constexpr (DEBUG) {
       static_assert(Sm::kIdx, "the candidate record needs the input indices");
       S.hidx[hb + i] = sm.inidx[i];
