@@ -56,15 +56,15 @@ struct TrkSoA {
 // fused track stage reads it) and its input index (candidate record only); a
 // stage without them holds more frames in flight per SM.  Triplets of a stage of
 // at most 256 hits are kept as 8-bit indices.
-template <int CH, int CT, int CK, int CC, bool PHI = true, bool IDX = true, int CH32 = (CH <= W_HITS ? CH : 1)>
+template <int CH, int CT, int CK, int CC, bool PHI = true, bool IDX = true, bool ADDR = true,
+          int CH32 = (CH <= W_HITS ? CH : 1)>
 struct FrameSm {
-  static constexpr bool kPhi = PHI, kIdx = IDX;
+  static constexpr bool kPhi = PHI, kIdx = IDX, kAddr = ADDR;
   static constexpr bool kPackB = CH < 256;  // bucket cursors as bytes, four to a word
   using TripT = typename std::conditional<(CH <= 256), uchar4, ushort4>::type;
   float x[CH], y[CH], z[CH], phi[PHI ? CH : 1];
-  uint32_t addr[CH];
+  uint32_t addr[ADDR ? CH : 1];
   uint16_t inidx[IDX ? CH : 1];
-  uint8_t bin[CH];
   uint16_t bstart[NBK + 1];
   uint32_t bcur[kPackB ? NBK / 4 : NBK];  // bucket counts, then cursors
   // warp stage, selection cuts: Phi01 / Phi12 partners of the layer-1 hits (regions
@@ -666,6 +666,19 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
 // ------------------------------------------------------------------ one frame
 
 
+// The phi bin of sorted layer-1 hit i: the last bin whose start is at most i (bins
+// are in order; an empty bin shares its start with the next one).
+__device__ __forceinline__ int layer1_bin(const uint16_t* bstart, int i) {
+  int lo = 0, hi = NB - 1;
+#pragma unroll
+  for (int step = 0; step < 5; ++step) {  // NB = 32
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)bstart[NB + mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Add one hit to bucket key; returns the bucket's count (cursor) before it.  With
 // packed cursors a bucket is one byte of a word: counts and starts stay below the
 // 256 hits such a frame can hold, so no byte carries into the next.
@@ -782,9 +795,8 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     sm.y[pos] = cl.y;
     if constexpr (S::kPhi) sm.phi[pos] = cl.z;
     sm.z[pos] = __ldg(P.row_lut + C.row_off[d.L] + d.row);
-    sm.addr[pos] = a;
+    if constexpr (S::kAddr) sm.addr[pos] = a;
     if constexpr (S::kIdx) sm.inidx[pos] = (uint16_t)i;
-    sm.bin[pos] = (uint8_t)d.b;
   }
   g.sync();
 
@@ -814,7 +826,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
         if (j < n1) {
           x1 = sm.x[i1];
           y1 = sm.y[i1];
-          const int b1 = sm.bin[i1];
+          const int b1 = layer1_bin(sm.bstart, i1);
           const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
           const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
           a0 = sm.bstart[s0];
@@ -973,7 +985,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
       for (int i1 = l1a + wid; i1 < l1b; i1 += NW) {
         if (overflowed()) break;
         const float x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
-        const int b1 = sm.bin[i1];
+        const int b1 = layer1_bin(sm.bstart, i1);
         const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
         const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
         const int a0 = sm.bstart[s0], n0a = sm.bstart[min(s0 + nb0, NB)] - a0;

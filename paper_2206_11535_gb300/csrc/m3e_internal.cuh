@@ -16,7 +16,7 @@ constexpr int DEFERRED = -1;      // process_frame result: frame too large for t
 // typical frames; anything above its capacities is re-run by the CTA stage,
 // whose capacities are the configuration limits.
 constexpr int W_HITS = 160, W_TRIP = 160, W_TRK = 48, W_COMBO = 512;
-constexpr int W_P01 = 512, W_P12 = 1024;  // warp stage: Phi-cut partner lists
+constexpr int W_P01 = 384, W_P12 = 1024;  // warp stage: Phi-cut partner lists
 constexpr int C_HITS = 4096, C_TRIP = 1024, C_TRK = 128, C_COMBO = 1024;
 constexpr int WARPS_PER_CTA = 4;  // persistent warp kernel: warps (frames in flight) per CTA
 constexpr int CTA_THREADS = 256;  // large-frame kernel

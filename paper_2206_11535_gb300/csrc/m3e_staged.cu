@@ -18,7 +18,8 @@ namespace {
 
 constexpr int NL3 = NB + 1;                        // layer-3 bin starts per frame
 constexpr int S1_TRIP = 160;                       // stage-1 warp-tier triplet capacity
-using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1, false, false>;  // phi re-read at emit, no input indices
+// phi re-read at emit; input indices instead of addresses (emit re-reads the few it needs)
+using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1, false, true, false>;
 using SmFrontD = FrameSm<W_HITS, S1_TRIP, 1, 1>;                // candidate record: with input indices
 constexpr int M_HITS = 1024;                       // stage-1 middle tier (CTA per frame)
 using SmFrontMid = FrameSm<M_HITS, C_TRIP, 1, 1>;
@@ -46,7 +47,7 @@ __device__ __forceinline__ int warp_count_add(int* ctr, bool pred) {  // ordered
 // ---- stage 1: write-out of a frame whose cuts selected triplets
 // Sorted hits and triplets go to global memory at places taken from the hit and
 // triplet allocators; a frame that does not fit is deferred (returns false).
-template <class G, class Sm, bool DEBUG>
+template <class G, class Sm, bool DEBUG, bool LIVE = false>
 __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, const KParams& P, const SParams& S,
                                            int f, int n, int ntrip, long long* bcast) {
   if (g.leader()) {
@@ -63,16 +64,20 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, 
   }
   // phi and the address of a sorted hit serve only the layer-3 search of stage 2
   const int l3s = sm.bstart[3 * NB];
+  const int32_t* hin = P.hits + (P.off[f] - P.off_base);
   for (int i = g.rank(); i < n; i += G::N) {
     float phi = 0.f;
     if (i >= l3s) {
+      uint32_t a;
+      if constexpr (Sm::kAddr) a = sm.addr[i];
+      else a = (uint32_t)(LIVE ? __ldcv(hin + sm.inidx[i]) : __ldg(hin + sm.inidx[i]));
       if constexpr (Sm::kPhi) {
         phi = sm.phi[i];
       } else {
-        const Dec d = decode(C, sm.addr[i]);
+        const Dec d = decode(C, a);
         phi = __ldg(P.col_lut + C.col_off[d.L] + d.g).z;
       }
-      S.haddr[hb + i] = sm.addr[i];
+      S.haddr[hb + i] = a;
     }
     S.hp[hb + i] = make_float4(sm.x[i], sm.y[i], sm.z[i], phi);
     if constexpr (DEBUG) {
@@ -96,14 +101,14 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, 
 }
 
 // After frame_front: decide, emit, or defer one frame (stage-1 tiers).
-template <class G, class Sm, bool DEBUG>
+template <class G, class Sm, bool DEBUG, bool LIVE = false>
 __device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const DevCfg& C, const KParams& P, const SParams& S,
                                               int f, int r, long long* bcast) {
   const int ntrip = sm.ntrip;
   if (r == PENDING && ntrip == 0) r = M3E_DROP;  // no triplet: no track, no vertex
   if (r == PENDING) {
     const int n = (int)(P.off[f + 1] - P.off[f]);
-    if (emit_frame<G, Sm, DEBUG>(g, sm, C, P, S, f, n, ntrip, bcast)) {
+    if (emit_frame<G, Sm, DEBUG, LIVE>(g, sm, C, P, S, f, n, ntrip, bcast)) {
       if (g.leader() && P.stats)
         for (int k = 0; k < ST_REASON0; ++k) sm.acc[k] += sm.facc[k];
     } else {
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
         }
       }
       const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED>(g, sm, C, P, f);
-      stage1_finish<WarpGroup, Sm, DEBUG>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
+      stage1_finish<WarpGroup, Sm, DEBUG, GATED>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
     }
   }
   flush_stats(g, sm, P.stats);
