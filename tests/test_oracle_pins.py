@@ -519,3 +519,23 @@ def test_signal_momenta_at_vertex(cfg, ocfg):
                 assert np.allclose(np.array(cb.pvec[j]), want, atol=1e-8 * p)
                 n += 1
     assert n > 60
+
+
+def test_fourth_hit_tie_goes_to_the_smaller_address(ocfg):
+    """Closest layer-3 hit (Sec. "Track Reconstruction"): with two layer-3 hits at the
+    same position the metrics tie exactly, and the smaller address wins (in the
+    positions form a hit's address is its layer and input index), whichever copy is
+    the track's own hit."""
+    d = gen.generate(40, 10, 0.0, None, seed=23, ms=True, digitise=False, noise=False)
+    checked = 0
+    for _, pos in _truth_tracks(d):
+        p = np.vstack([pos, pos[3]])
+        o = O.select_frame(ocfg, [0, 1, 2, 3, 3], positions=p)
+        trk = [t for t in o["tracks"] if tuple(t.i[:3]) == (0, 1, 2)]
+        if not trk or trk[0].status < 3:  # the triplet failed a cut, or no layer-3 crossing
+            continue
+        t = trk[0]
+        assert t.m_best == t.m_second
+        assert t.i[3] == 3
+        checked += 1
+    assert checked > 40
