@@ -539,3 +539,59 @@ def test_fourth_hit_tie_goes_to_the_smaller_address(ocfg):
         assert t.i[3] == 3
         checked += 1
     assert checked > 40
+
+
+def test_vertex_z_is_the_inverse_variance_mean(ocfg):
+    """Vertex z and chi2 (Sec. "Vertex Fit": mu_z the error-weighted mean of the z_i,
+    chi2 the weighted sum of squared residuals): an exact signal decay with one track
+    moved rigidly along z by delta keeps its transverse geometry, so chi2 = delta^2
+    w_k (W - w_k) / W and mu_z moves by delta w_k / W.  The weights recovered from the
+    three single-track moves must agree with each other (W three times, and the sum
+    of the w_k), and chi2 must grow as delta^2."""
+    d = gen.generate(60, 0.0, 0.0, 1, seed=27, ms=False, digitise=False, noise=False)
+    delta = 0.05
+    checked = 0
+    for f in range(60):
+        a, b = d["off"][f], d["off"][f + 1]
+        ht = d["hit_track"][a:b]
+        tracks = sorted({int(t) for t in ht if t >= 0})
+        if len(tracks) != 3:
+            continue
+        vz = d["trk_vz"][tracks[0]]
+
+        def truth_combo(pos):
+            o = O.select_frame(ocfg, d["hit_layer"][a:b], positions=pos)
+            kt = {}
+            for ki, ti in enumerate(o["kept"]):
+                owners = {int(ht[i]) for i in o["tracks"][ti].i}
+                if len(owners) == 1:
+                    kt[ki] = owners.pop()
+            for cb in o["combos"]:
+                if all(t in kt for t in cb.t) and len({kt[t] for t in cb.t}) == 3 and cb.status == 2:
+                    return cb
+            return None
+
+        w, W = [], []
+        for tr in tracks:
+            res = []
+            for s in (delta, 2 * delta):
+                pos = d["hit_pos"][a:b].copy()
+                pos[ht == tr, 2] += s
+                res.append(truth_combo(pos))
+            if any(r is None for r in res):
+                break
+            c1, c2 = res
+            assert c1.chi2 > 1e-3  # delta = 50 um against z errors of ~0.1 mm
+            assert c2.chi2 == pytest.approx(4 * c1.chi2, rel=1e-6, abs=0)
+            fk = (c1.mu[2] - vz) / delta
+            assert 0.0 < fk < 1.0
+            wk = c1.chi2 / (delta * delta * (1.0 - fk))
+            w.append(wk)
+            W.append(wk / fk)
+        if len(w) != 3:
+            continue
+        assert W[1] == pytest.approx(W[0], rel=1e-5, abs=0) and W[2] == pytest.approx(W[0], rel=1e-5, abs=0)
+        assert sum(w) == pytest.approx(W[0], rel=1e-5, abs=0)
+        assert max(w) > 1.05 * min(w)  # unequal weights: an unweighted mean would fail above
+        checked += 1
+    assert checked > 10
