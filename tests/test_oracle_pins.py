@@ -595,3 +595,22 @@ def test_vertex_z_is_the_inverse_variance_mean(ocfg):
         assert max(w) > 1.05 * min(w)  # unequal weights: an unweighted mean would fail above
         checked += 1
     assert checked > 10
+
+
+def test_target_filter_margin_only_adds_points(cfg):
+    """Target filter (Sec. "Vertex Fit"; the margin beyond the target radius is a
+    reading): a wider margin keeps every intersection point a narrower one keeps, so
+    every combination vertexed without margin is vertexed with it, and on background
+    frames the margin adds some."""
+    d = gen.workload("c2", n_frames=60)
+    c0 = O.make_config(cfg, isect_margin=0.0)
+    c2 = O.make_config(cfg, isect_margin=2.0)
+    added = 0
+    for f in range(60):
+        fr = d["hits"][d["off"][f]:d["off"][f + 1]]
+        o0, o2 = O.select_frame(c0, fr), O.select_frame(c2, fr)
+        v0 = {tuple(cb.t) for cb in o0["combos"] if cb.status == 2}
+        v2 = {tuple(cb.t) for cb in o2["combos"] if cb.status == 2}
+        assert v0 <= v2
+        added += len(v2 - v0)
+    assert added > 0
