@@ -197,6 +197,27 @@ def cpu_baseline(d, seconds_target=12.0):
                       f"disjoint frame ranges, brute force over every hit triplet ({dt:.1f} s)"}
 
 
+def parity_sample(ctx, d, dev, n_frames=2000):
+    """Part of the CPU-baseline leg: the first n_frames frames of the batch through the
+    staged form with its candidate record, compared candidate by candidate with the
+    oracle; frames that match, differ only inside a boundary band (counted per band),
+    or fail."""
+    import torch
+    from oracle import oracle as O
+    from paper_2206_11535_gb300 import gen
+    from tests import parity
+    nf = min(n_frames, d["off"].size - 1)
+    hits = d["hits"][:d["off"][nf]]
+    off = d["off"][:nf + 1]
+    rec = ctx.select_frames_debug(torch.from_numpy(hits).to(dev), torch.from_numpy(off).to(dev),
+                                  cap_trip=1024, cap_combo=1024)
+    rec = {k: v.cpu().numpy() for k, v in rec.items()}
+    res = parity.compare_batch(O.make_config(gen.load_config()), hits, off, rec)
+    return {"frames": nf, "form": "staged", **parity.summary(res),
+            "boundary_differences_per_band": parity.band_counts(res),
+            "bands": dict(parity.BAND), "oracle": "FP64 C oracle, candidate by candidate"}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
     if rank != 0:
@@ -586,6 +607,7 @@ def main():
            "roofline": roof, "e2e": e2e, "clocks": cl, "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(d)
+        out["parity"] = parity_sample(ctx, d, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()

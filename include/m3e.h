@@ -130,6 +130,12 @@ typedef struct {
                               status | pass << 8 (status 0 no intersection, 1 emptied by the
                               target filter, 2 vertexed) */
   float* combo_val;        /* [F][cap_combo][4] energy sum - m_mu, chi2, target distance, |sum p| */
+  float* combo_aux;        /* [F][cap_combo][4] or NULL: the values that decide the vertex status and
+                              choice, for the boundary bands of a parity check: smallest relative
+                              discriminant |h^2|/r_a^2 of the three circle pairs, smallest distance
+                              (mm) of an intersection point from target_r + isect_margin, the
+                              second-smallest chi2 over the intersection choices, 0 (FLT_MAX where
+                              the vertex stopped before the quantity) */
 } m3e_dump;
 
 typedef struct m3e_ctx m3e_ctx;
@@ -248,6 +254,24 @@ int m3e_set_profiling(m3e_ctx* ctx, int on);
 int m3e_kernel_times(m3e_ctx* ctx, float* main_ms, float* deferred_ms);
 int m3e_stage_times(m3e_ctx* ctx, float* ms, int n);
 
+/* Hit ingest (Sec. "Memory Layout": hits as points (x, y, z), loaded per frame
+ * for the selection; Sec. "Selection Cuts": the azimuth phi the cuts bin on):
+ * decodes n_hits packed int32 pixel addresses into FP32 coordinates, as
+ * structure of arrays, through the context's look-up tables (built in FP64,
+ * rounded once), so every value equals the FP64 pixel centre rounded once to FP32:
+ *   x = r_L cos(phi), y = r_L sin(phi), z = -H_L + (row + 1/2) pitch   [mm],
+ *   phi = (ladder * n_cols_L + col + 1/2) 2 pi / (n_ladders_L n_cols_L) [rad].
+ * d_hits [n_hits] and d_x, d_y, d_z, d_phi [n_hits] are caller-owned DEVICE
+ * arrays; d_phi may be NULL (not written).  Hits keep their order (hit i of the
+ * input is element i of each output); a frame's hits are a contiguous range, so
+ * the frame offsets of the selection apply unchanged.  An invalid address gives
+ * NaN in every output of that hit and latches M3E_EBADHIT (m3e_check).  One
+ * kernel launch on `stream`; 16-byte-aligned arrays take the vectorised path.
+ * The selection entry points do not need this call (they decode as they load a
+ * frame); it serves callers that want the decoded hits themselves. */
+int m3e_ingest(m3e_ctx* ctx, const int32_t* d_hits, int64_t n_hits, float* d_x, float* d_y, float* d_z,
+               float* d_phi, cudaStream_t stream);
+
 /* Selection without any device allocation in the call (the paper has no
  * counterpart; this is a deployment aid).  Same decisions as m3e_select_frames,
  * through the fused kernels, with their scratch in a fixed static device array
@@ -258,7 +282,11 @@ int m3e_stage_times(m3e_ctx* ctx, float* ms, int n);
  * exist already (m3e_create allocates; create it during initialisation).
  *   - At most 262,144 frames per call; more returns M3E_EINVAL.
  *   - The first call on a device looks up the array's device address (set-up);
- *     make that first call before any stream capture.
+ *     make that first call before any stream capture.  The address is cached per
+ *     device; m3e_create clears the cache, so after a cudaDeviceReset create a
+ *     new context before calling again.
+ *   - Frames above the context's warp-tier size (set by m3e_autotune)
+ *     go to the CTA-per-frame kernel, as in m3e_select_frames_fused.
  *   - The array is shared by all calls on a device and keeps the last call's
  *     contents; the call clears what must start at zero.  Calls that overlap on
  *     the GPU (other streams, other contexts of the same device, other threads)

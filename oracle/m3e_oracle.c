@@ -66,6 +66,7 @@ int orc_decode(const orc_config* c, uint32_t addr, orc_hit* h) {
   h->x = c->r[L] * cos(phi);
   h->y = c->r[L] * sin(phi);
   h->z = -c->H[L] + ((double)row + 0.5) * c->pitch;
+  h->phi = phi;
   h->layer = L; h->ladder = lad; h->col = col; h->row = row;
   h->addr = addr;
   return 0;
@@ -431,6 +432,25 @@ static void vertex_combination(const orc_config* c, const vtrack* V[3], orc_comb
   rec->chi2 = INFINITY; rec->chi2_second = INFINITY; rec->tdist = INFINITY; rec->ptot = INFINITY;
   rec->disc_min = INFINITY; rec->filt_margin = INFINITY;
   double lim = c->target_r + c->isect_margin;
+  /* Diagnostics for a comparison with another implementation (no decision uses
+   * them): over all three pairs, whatever the status, the smallest squared half
+   * chord relative to the product of the two radii (how close a pair is to not
+   * meeting) and the smallest distance of an intersection point from the filter
+   * radius.  Both are symmetric in the tracks, hence independent of their order. */
+  for (int k = 0; k < 3; k++) {
+    const vtrack* A = V[pr[k][0]];
+    const vtrack* B = V[pr[k][1]];
+    double ex = B->cx - A->cx, ey = B->cy - A->cy;
+    double D = hypot(ex, ey);
+    if (!(D > 0)) continue;
+    double a = (A->rt * A->rt - B->rt * B->rt + D * D) / (2.0 * D);
+    double h2 = A->rt * A->rt - a * a;
+    rec->disc_min = fmin(rec->disc_min, fabs(h2) / (A->rt * B->rt));
+    if (h2 < 0) continue;
+    double h = sqrt(h2), bx = A->cx + a * ex / D, by = A->cy + a * ey / D;
+    rec->filt_margin = fmin(rec->filt_margin, fabs(hypot(bx - h * ey / D, by + h * ex / D) - lim));
+    if (h2 > 0) rec->filt_margin = fmin(rec->filt_margin, fabs(hypot(bx + h * ey / D, by - h * ex / D) - lim));
+  }
   for (int k = 0; k < 3; k++) {
     const vtrack* A = V[pr[k][0]];
     const vtrack* B = V[pr[k][1]];
@@ -440,7 +460,6 @@ static void vertex_combination(const orc_config* c, const vtrack* V[3], orc_comb
     if (!(D > 0)) { rec->status = 0; return; }
     double a = (A->rt * A->rt - B->rt * B->rt + D * D) / (2.0 * D);
     double h2 = A->rt * A->rt - a * a;
-    rec->disc_min = fmin(rec->disc_min, fabs(h2) / (A->rt * A->rt));
     if (h2 < 0) { rec->status = 0; return; }
     ex /= D; ey /= D;
     double bx = A->cx + a * ex, by = A->cy + a * ey;
@@ -455,7 +474,6 @@ static void vertex_combination(const orc_config* c, const vtrack* V[3], orc_comb
     }
     for (int j = 0; j < nc; j++) {
       double rr = hypot(cand[j][0], cand[j][1]);
-      rec->filt_margin = fmin(rec->filt_margin, fabs(rr - lim));
       if (rr > lim) continue;
       pts[k][npt[k]][0] = cand[j][0]; pts[k][npt[k]][1] = cand[j][1];
       var[k][npt[k]] = point_var(c, A, cand[j][0], cand[j][1]) + point_var(c, B, cand[j][0], cand[j][1]);

@@ -38,6 +38,7 @@ typedef struct {          /* one decoded hit */
   int32_t layer, ladder, col, row;
   uint32_t addr;
   int32_t in_idx;
+  double phi;             /* azimuth of the pixel column centre, [0, 2 pi) (decode only) */
 } orc_hit;
 
 typedef struct {          /* result of the single triplet fit (Sec. Track Reconstruction) */
@@ -69,8 +70,8 @@ typedef struct {          /* one e+ e+ e- combination that passed the energy tes
   int32_t pass;           /* 1 when the three signal cuts pass */
   double chi2, tdist, ptot;
   double chi2_second;     /* second-smallest chi2 over intersection choices (or inf) */
-  double disc_min;        /* smallest relative discriminant h^2/r^2 over the three pairs */
-  double filt_margin;     /* smallest | |p| - (target_r + margin) | over candidate points */
+  double disc_min;        /* smallest |h^2| / (r_a r_b) over the three pairs (h: half chord) */
+  double filt_margin;     /* smallest | |p| - (target_r + margin) | over all intersection points */
   double mu[3];
   double pvec[3][3];      /* momentum of each track at its closest point (MeV) */
 } orc_combo_rec;

@@ -46,7 +46,7 @@ class Config(C.Structure):
 class Hit(C.Structure):
     _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double),
                 ("layer", C.c_int32), ("ladder", C.c_int32), ("col", C.c_int32), ("row", C.c_int32),
-                ("addr", C.c_uint32), ("in_idx", C.c_int32)]
+                ("addr", C.c_uint32), ("in_idx", C.c_int32), ("phi", C.c_double)]
 
 
 class TFit(C.Structure):

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libm3e.so")
-UNITS = ["m3e_staged.cu", "m3e_fused.cu", "m3e_stream.cu", "m3e_grad.cu", "m3e_abi.cu"]
+UNITS = ["m3e_staged.cu", "m3e_fused.cu", "m3e_stream.cu", "m3e_grad.cu", "m3e_ingest.cu", "m3e_abi.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "--prec-div=false", "--prec-sqrt=false", "-ftz=false", "--fmad=true",

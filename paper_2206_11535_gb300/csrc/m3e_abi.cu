@@ -13,6 +13,8 @@
 
 using namespace m3e;
 
+void noalloc_forget(int dev);  // defined with m3e_select_frames_noalloc below
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -90,7 +92,7 @@ struct Scratch {
 struct m3e_ctx {
   int device = 0;
   int sms = 1;
-  int fused_bpsm = 1, s1_bpsm = 1, s2_bpsm = 1, s3_bpsm = 1, s4_bpsm = 1, s1c_bpsm = 1, s1m_bpsm = 1;
+  int fused_bpsm = 1, s1_bpsm = 1, s2_bpsm = 1, s3_bpsm = 1, s4_bpsm = 1, s1c_bpsm = 1, s1m_bpsm = 1, ingest_bpsm = 1;
   int grab = 4;
   int defer_hits = W_HITS;
   m3e_config cfg{};
@@ -178,9 +180,16 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
     co += d.ntot[L];
     ro += d.nrow[L];
   }
+  for (int L = 0; L < 4; ++L) {
+    const double st = TWO_PI / d.ntot[L];
+    d.phs_hi[L] = (float)st;
+    d.phs_lo[L] = (float)(st - (double)d.phs_hi[L]);
+  }
   d.inv_dr01 = (float)(1.0 / (c.r_mm[1] - c.r_mm[0]));
   d.inv_dr12 = (float)(1.0 / (c.r_mm[2] - c.r_mm[1]));
   d.dr12 = (float)(c.r_mm[2] - c.r_mm[1]);
+  d.zoff2 = (float)c.half_len_mm[2];
+  d.izw2 = (float)(NB / (2.0 * c.half_len_mm[2]));
   d.c01 = (float)(std::cos(c.phi01_max) * c.r_mm[0] * c.r_mm[1]);
   d.c12 = (float)(std::cos(c.phi12_max) * c.r_mm[1] * c.r_mm[2]);
   d.dl_max = (float)c.dlambda_max;
@@ -420,6 +429,7 @@ int m3e_create(const m3e_config* cfg, int cuda_device, m3e_ctx** out) {
   x->device = cuda_device;
   x->cfg = *cfg;
   make_devcfg(*cfg, x->dc);
+  noalloc_forget(cuda_device);
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, cuda_device) != cudaSuccess) {
     delete x;
@@ -433,6 +443,7 @@ int m3e_create(const m3e_config* cfg, int cuda_device, m3e_ctx** out) {
   x->s4_bpsm = stage_blocks_per_sm(4);
   x->s1c_bpsm = stage_blocks_per_sm(5);
   x->s1m_bpsm = stage_blocks_per_sm(6);
+  x->ingest_bpsm = ingest_blocks_per_sm();
   // look-up tables in FP64, rounded once
   int ncolt = 0, nrowt = 0;
   for (int L = 0; L < 4; ++L) {
@@ -724,6 +735,23 @@ int m3e_set_host_pipeline(m3e_ctx* x, int max_chunks, int wait_ms, int drop_chun
 
 }  // extern "C"
 
+// ------------------------------------------------------------------ hit ingest
+
+extern "C" int m3e_ingest(m3e_ctx* x, const int32_t* d_hits, int64_t n_hits, float* d_x, float* d_y, float* d_z,
+                          float* d_phi, cudaStream_t s) {
+  if (!x) return fail(M3E_EINVAL, "ctx is NULL");
+  if (n_hits < 0) return fail(M3E_EINVAL, "n_hits < 0");
+  x->last_launches = 0;
+  x->prof_valid = false;
+  if (n_hits == 0) return M3E_OK;
+  if (!d_hits || !d_x || !d_y || !d_z) return fail(M3E_EINVAL, "NULL hit or coordinate array");
+  DeviceGuard guard(x->device);
+  CUDA_TRY(launch_ingest(x->dc, d_hits, n_hits, x->col_lut, x->row_lut, d_x, d_y, d_z, d_phi, x->err,
+                         x->sms * x->ingest_bpsm, s));
+  x->last_launches = 1;
+  return M3E_OK;
+}
+
 // ------------------------------------------------------------------ selection without allocation
 //
 // m3e_select_frames_noalloc runs the fused kernels with their scratch (work-queue
@@ -763,6 +791,15 @@ int noalloc_scratch(int dev, int** out) {
 
 }  // namespace
 
+// Forget the cached address of `dev` so that the next call looks it up again: a
+// context created after the device's primary context was reset
+// (cudaDeviceReset) sees the array at its new address.
+void noalloc_forget(int dev) {
+  if (dev < 0 || dev >= 256) return;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  g_noalloc_ptr[dev] = nullptr;
+}
+
 extern "C" int m3e_select_frames_noalloc(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_frame_off,
                                          int64_t n_frames, uint8_t* d_keep, uint8_t* d_reason, cudaStream_t s) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
@@ -787,7 +824,7 @@ extern "C" int m3e_select_frames_noalloc(m3e_ctx* x, const int32_t* d_hits, cons
   p.defer_count = scratch + 1;
   p.in_list = scratch + NOALLOC_HEAD;
   p.in_count = scratch + 1;
-  p.defer_hits = W_HITS;
+  p.defer_hits = x->defer_hits;  // the same warp/CTA split as the fused entry point
   p.grab = x->grab;
   p.hits = d_hits;
   p.off = d_frame_off;

@@ -67,13 +67,13 @@ struct FrameSm {
   uint16_t inidx[IDX ? CH : 1];
   uint16_t bstart[NBK + 1];
   uint32_t bcur[kPackB ? NBK / 4 : NBK];  // bucket counts, then cursors
-  // warp stage, selection cuts: Phi01 / Phi12 partners of the layer-1 hits (regions
-  // r01 / r12, counts c12) and the start of each layer-1 hit's candidate triplets
-  uint8_t p01[CH32 == 1 ? 1 : W_P01], p12[CH32 == 1 ? 1 : W_P12];
-  uint16_t r01[CH32], r12[CH32];
-  uint8_t c12[CH32];
-  uint8_t own[CH32 == 1 ? 1 : 32];  // warp stage, part C: layer-1 hit of each pair of a round
-  uint16_t cst[CH32 + 1];
+  // warp stage, selection cuts (warp_cuts): Phi01 partners of a chunk of 32 layer-1
+  // hits, the layer-2 hits in z-bin order (zidx, bin starts zbs) and the candidate
+  // triplets of one round of (layer-1 hit, Phi01 partner) pairs
+  uint8_t p01[CH32 == 1 ? 1 : W_P01];
+  uint8_t zidx[CH32 == 1 ? 1 : W_L2];
+  uint8_t zbs[CH32 == 1 ? 1 : NB + 1];
+  alignas(16) uint16_t cand[CH32 == 1 ? 1 : W_CAND];  // also the z-bin counters (32-bit words)
   TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
     TripT trip[CT];             // selected triplets (sorted-hit indices)
@@ -88,6 +88,16 @@ using SmWarp = FrameSm<W_HITS, W_TRIP, W_TRK, W_COMBO>;
 using SmCta = FrameSm<C_HITS, C_TRIP, C_TRK, C_COMBO>;
 
 // ------------------------------------------------------------------ small helpers
+
+// Asynchronous 4-byte copy from global to shared memory (no register holds the
+// value), and the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 template <class T>
 __device__ __forceinline__ T make_trip(int i0, int i1, int i2) {  // a triplet of sorted-hit indices
@@ -154,22 +164,14 @@ struct SegF {
 };
 
 // One segment of the circle solution: chord d, axial length z, transverse radius
-// Rct of the circle through the triplet.  Helix relations d = 2 R_t sin(Phi/2),
-// z = R_t Phi cot(theta), R_t = R sin(theta) give the 3D radius R_C, the polar
-// angle theta_C and the derivatives dPhi/dR, dtheta/dR at the circle solution.
-// sin(Phi/2) = d / 2R_t on either arc (the long arc turns by 2 pi minus the short
-// one, which leaves the sine of the half angle and flips its cosine).
-// inv2R = 1 / (2 R_t).  The divisions share the reciprocals of Phi and of
+// Rct of the circle through the triplet, and the arc angle Phi travelled along the
+// segment with sh = sin(Phi/2) and ch = cos(Phi/2).  Helix relations
+// d = 2 R_t sin(Phi/2), z = R_t Phi cot(theta), R_t = R sin(theta) give the 3D
+// radius R_C, the polar angle theta_C and the derivatives dPhi/dR, dtheta/dR at
+// the circle solution.  The divisions share the reciprocals of Phi and of
 // sin(Phi/2): dPhi/dR = -R_C / (d^2 cos(Phi/2) / (8 sin^3(Phi/2)) + zp^2 / Phi).
-__device__ __forceinline__ SegF segment(float d, float z, float Rct, float inv2R, bool obtuse) {
+__device__ __forceinline__ SegF segment_core(float d, float z, float Rct, float sh, float ch, float ph) {
   SegF s;
-  const float sh = fminf(1.f, d * inv2R);
-  float ph = 2.f * asinf(sh);
-  float ch = sqrtf(fmaxf((1.f - sh) * (1.f + sh), 0.f));
-  if (obtuse) {
-    ph = TWO_PI_F - ph;
-    ch = -ch;
-  }
   const float iph = 1.f / ph, ish = 1.f / sh;
   const float zp = z * iph;
   s.RC = sqrtf(Rct * Rct + zp * zp);
@@ -183,6 +185,23 @@ __device__ __forceinline__ SegF segment(float d, float z, float Rct, float inv2R
   s.phi = ph;
   s.zp = zp;
   return s;
+}
+
+// The same from the chord alone: sin(Phi/2) = d / 2R_t on either arc (the long arc
+// turns by 2 pi minus the short one, which leaves the sine of the half angle and
+// flips its cosine); inv2R = 1 / (2 R_t).  Near a half turn (d -> 2 R_t) the arc
+// sine loses half the digits of its argument; the triplet fit therefore takes the
+// angle from the triangle (fit_triplet), and this form serves the reverse sweep of
+// the alignment gradient, which differentiates it.
+__device__ __forceinline__ SegF segment(float d, float z, float Rct, float inv2R, bool obtuse) {
+  const float sh = fminf(1.f, d * inv2R);
+  float ph = 2.f * asinf(sh);
+  float ch = sqrtf(fmaxf((1.f - sh) * (1.f + sh), 0.f));
+  if (obtuse) {
+    ph = TWO_PI_F - ph;
+    ch = -ch;
+  }
+  return segment_core(d, z, Rct, sh, ch, ph);
 }
 
 struct TFitF {
@@ -220,11 +239,19 @@ __device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx
   f.eps = rtc > 0.f ? 1.f : -1.f;
   f.ccx = bx + (vy * u2 - uy * v2) * i2c;
   f.ccy = by + (ux * v2 - vx * u2) * i2c;
-  const float inv2R = 0.5f / f.Rct;
-  const bool ob0 = ((ax - cx) * (bx - cx) + (ay - cy) * (by - cy)) < 0.f;
-  const bool ob1 = ((bx - ax) * (cx - ax) + (by - ay) * (cy - ay)) < 0.f;
-  const SegF s0 = segment(d01, bz - az, f.Rct, inv2R, ob0);
-  const SegF s1 = segment(d12, cz - bz, f.Rct, inv2R, ob1);
+  // Arc angle of each segment from the triangle: the track's arc from a to b is
+  // the one that does not hold c, so it turns by twice the inscribed angle at c,
+  // Phi01 = 2 atan2(|cross|, (a - c).(b - c)) (more than pi when that angle is
+  // obtuse), and Phi12 likewise by twice the angle at a.  sin(Phi/2) and
+  // cos(Phi/2) are that angle's sine and cosine, |cross| / (lengths) and
+  // dot / (lengths): full precision up to a half turn and beyond, where the arc
+  // sine of d / 2R_t would lose half its digits.
+  const float acr = fabsf(cross);
+  const float dotc = (ax - cx) * (bx - cx) + (ay - cy) * (by - cy);
+  const float dota = (bx - ax) * (cx - ax) + (by - ay) * (cy - ay);
+  const float il0 = 1.f / (d20 * d12), il1 = 1.f / (d01 * d20);
+  const SegF s0 = segment_core(d01, bz - az, f.Rct, acr * il0, dotc * il0, 2.f * atan2f(acr, dotc));
+  const SegF s1 = segment_core(d12, cz - bz, f.Rct, acr * il1, dota * il1, 2.f * atan2f(acr, dota));
   const float dR = s0.RC - s1.RC;
   f.Rref = s0.RC;
   f.alpha = 0.5f * (s0.dphi + s1.dphi);
@@ -510,6 +537,7 @@ __device__ __forceinline__ bool pz_fails_ptot(float Pz, float ptot_max) {
 struct VtxOut {
   int status, pass;
   float chi2, tdist, ptot;
+  float chi2_second;  // second-smallest chi2 over the choices (candidate record only)
 };
 
 // Whether the transverse circles (centre, radius) of two tracks intersect, with
@@ -545,6 +573,32 @@ __device__ __forceinline__ bool pair_geometry(float acx, float acy, float ar, fl
   k0 = sqrtf(x0 * x0 + y0 * y0) <= lim;
   k1 = h2 != 0.f && sqrtf(x1 * x1 + y1 * y1) <= lim;
   return true;
+}
+
+// The quantities that decide the geometric steps of the vertex, over all three
+// pairs whatever the status (candidate record only, for the boundary bands of a
+// parity check): the smallest squared half chord relative to the product of the
+// two radii, and the smallest distance of an intersection point from the filter
+// radius.  Symmetric in the tracks, so independent of their order.
+__device__ __forceinline__ void vertex_soft(const TrackR& A, const TrackR& B, const TrackR& E, float lim, float& disc,
+                                            float& margin) {
+  disc = margin = FLT_MAX;
+  const TrackR* V[3] = {&A, &B, &E};
+#pragma unroll 1
+  for (int k = 0; k < 3; ++k) {
+    const TrackR& a = *V[k == 2 ? 1 : 0];
+    const TrackR& b = *V[k == 0 ? 1 : 2];
+    float D, aa, h2;
+    const bool meet = circles_meet(a.cx, a.cy, a.rt, b.cx, b.cy, b.rt, D, aa, h2);
+    if (!(D > 0.f)) continue;
+    disc = fminf(disc, fabsf(h2) / (a.rt * b.rt));
+    if (!meet) continue;
+    float x0, y0, x1, y1;
+    bool k0, k1;
+    pair_geometry(a.cx, a.cy, a.rt, b.cx, b.cy, b.rt, lim, x0, y0, k0, x1, y1, k1);
+    margin = fminf(margin, fabsf(sqrtf(x0 * x0 + y0 * y0) - lim));
+    if (h2 != 0.f) margin = fminf(margin, fabsf(sqrtf(x1 * x1 + y1 * y1) - lim));
+  }
 }
 
 // Status of a combination after the first two vertex steps: 0 a pair of circles
@@ -596,6 +650,7 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
   o.status = 0;
   o.pass = 0;
   o.chi2 = o.tdist = o.ptot = FLT_MAX;
+  o.chi2_second = FLT_MAX;
   float x00, y00, v00, x01, y01, v01, x10, y10, v10, x11, y11, v11, x20, y20, v20, x21, y21, v21;
   bool k00, k01, k10, k11, k20, k21;
   if (!pair_points(A, B, C, x00, y00, v00, k00, x01, y01, v01, k01)) return o;
@@ -634,11 +689,14 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
                        ((pb - mx) * (pb - mx) + (qb - my) * (qb - my) + (zb - mz) * (zb - mz)) * ib +
                        ((pe - mx) * (pe - mx) + (qe - my) * (qe - my) + (ze - mz) * (ze - mz)) * ie;
     if (!have || chi2 < best) {
+      if (have) o.chi2_second = best;
       have = true;
       best = chi2;
       bmx = mx;
       bmy = my;
       bmz = mz;
+    } else if (chi2 < o.chi2_second) {
+      o.chi2_second = chi2;
     }
   }
   if (!have || !isfinite(best)) return o;
@@ -665,6 +723,37 @@ __device__ __forceinline__ VtxOut vertex(const TrackR& A, const TrackR& B, const
 
 // ------------------------------------------------------------------ one frame
 
+
+// The exact cut tests, written with explicitly rounded operations so that every
+// stage and tier takes the same decision whatever the compiler contracts:
+// Phi cut between two hits: h_a . h_b >= cos(phi_max) r_a r_b.
+__device__ __forceinline__ bool phi_pass(float xa, float ya, float xb, float yb, float c) {
+  return fmaf(xa, xb, __fmul_rn(ya, yb)) >= c;
+}
+// Delta lambda: |tan(lambda12) - tan(lambda01)| <= dl_max, with tan(lambda01) given.
+__device__ __forceinline__ bool dl_pass(float z1, float z2, float tl01, const DevCfg& C) {
+  return fabsf(fmaf(__fsub_rn(z2, z1), C.inv_dr12, -tl01)) <= C.dl_max;
+}
+__device__ __forceinline__ float tan_l01(float z0, float z1, const DevCfg& C) {
+  return __fmul_rn(__fsub_rn(z1, z0), C.inv_dr01);
+}
+// r_tc window without division or root: (d01 d12 d20)^2 against (2 r cross)^2.
+__device__ __forceinline__ bool rtc_pass(float x0, float y0, float x1, float y1, float x2, float y2,
+                                         const DevCfg& C) {
+  const float ax = __fsub_rn(x0, x1), ay = __fsub_rn(y0, y1), bx = __fsub_rn(x2, x1), by = __fsub_rn(y2, y1);
+  const float cr = fmaf(ax, by, -__fmul_rn(ay, bx));
+  const float ex = __fsub_rn(x2, x0), ey = __fsub_rn(y2, y0);
+  const float Pq = __fmul_rn(__fmul_rn(fmaf(ax, ax, __fmul_rn(ay, ay)), fmaf(bx, bx, __fmul_rn(by, by))),
+                             fmaf(ex, ex, __fmul_rn(ey, ey)));
+  const float Qq = __fmul_rn(cr, cr);
+  return cr != 0.f && Pq >= __fmul_rn(C.rtc_lo2, Qq) && Pq <= __fmul_rn(C.rtc_hi2, Qq);
+}
+// z bin of a layer-2 point in the warp stage: monotone in z, so every hit with z in
+// [zlo, zhi] lies in bins zbin(zlo) .. zbin(zhi).
+__device__ __forceinline__ int zbin2(float z, const DevCfg& C) {
+  const int b = (int)__fmul_rn(__fadd_rn(z, C.zoff2), C.izw2);
+  return b < 0 ? 0 : (b > NB - 1 ? NB - 1 : b);
+}
 
 // The phi bin of sorted layer-1 hit i: the last bin whose start is at most i (bins
 // are in order; an empty bin shares its start with the next one).
@@ -728,6 +817,205 @@ __device__ __forceinline__ void bucket_scan(const G& g, S& sm) {
   g.sync();
 }
 
+// Selection cuts of a warp-stage frame (Algorithm 2), on the hits sorted by (layer,
+// phi bin).  The layer-2 hits are also put in z-bin order (at most W_L2 of them), so
+// that for a (layer-1 hit, Phi01 partner) pair the Delta lambda cut, seen as a z
+// window on the layer-2 hit, becomes a contiguous range of that order.  Per chunk
+// of 32 layer-1 hits (a lane each):
+//   1. the Phi01 partners within the reachable phi bins, stored in a region of p01
+//      reserved by a prefix sum of the window sizes;
+//   2. the Phi12 partners as a bit mask over the z-ordered layer-2 hits, from one
+//      pass over them that all lanes take together;
+//   3. the pairs, numbered by a prefix sum and taken 32 at a time: each lane finds
+//      its pair's layer-1 hit (a search over the lanes' prefix), forms the z window
+//      (widened by 1e-3 mm against rounding) and its bin range, and keeps the Phi12
+//      partners inside it: the candidate triplets, numbered by a prefix sum;
+//   4. the candidates, 32 at a time, through the exact Delta lambda and r_tc tests,
+//      the survivors appended in a fixed order by ballot.
+// The exact tests are the expressions every other stage uses (phi_pass, dl_pass,
+// rtc_pass), and the z window contains every hit that passes Delta lambda, so the
+// selected set equals the brute-force one.  sm.bad = 2 when a capacity is exceeded
+// (the frame goes to a larger stage).  npair / ntt: this lane's share of the pair
+// tests (within the reachable bins) and of the candidate triplets (Phi01 partners
+// times Phi12 partners), the statistics' counts.
+template <class S, int CT>
+__device__ __forceinline__ void warp_cuts(S& sm, const DevCfg& C, bool stats, unsigned& npair, unsigned& ntt) {
+  const int lane = threadIdx.x & 31;
+  const int l1a = sm.bstart[NB], l1b = sm.bstart[2 * NB], l2b = sm.bstart[3 * NB];
+  const int n1 = l1b - l1a, n2 = l2b - l1b;
+  const int nb0 = min(2 * C.k01 + 1, NB), nb2 = min(2 * C.k12 + 1, NB);
+  bool over = n2 > W_L2;
+  int nt = 0;
+  if (!over) {
+    // layer-2 hits in z-bin order: counting sort with byte counters packed four to a
+    // word (in the candidate buffer, free until step 3)
+    uint32_t* zc = reinterpret_cast<uint32_t*>(sm.cand);
+    if (lane < NB / 4) zc[lane] = 0u;
+    __syncwarp();
+    const int bq0 = lane < n2 ? zbin2(sm.z[l1b + lane], C) : -1;
+    const int bq1 = lane + 32 < n2 ? zbin2(sm.z[l1b + lane + 32], C) : -1;
+    if (bq0 >= 0) atomicAdd(&zc[bq0 >> 2], 1u << (8 * (bq0 & 3)));
+    if (bq1 >= 0) atomicAdd(&zc[bq1 >> 2], 1u << (8 * (bq1 & 3)));
+    __syncwarp();
+    const int cb = (int)((zc[lane >> 2] >> (8 * (lane & 3))) & 255u);
+    int inc = cb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t;
+    }
+    sm.zbs[lane] = (uint8_t)(inc - cb);
+    if (lane == 31) sm.zbs[NB] = (uint8_t)inc;
+    __syncwarp();
+    if (lane < NB / 4) {
+      uint32_t w = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w |= (uint32_t)sm.zbs[4 * lane + k] << (8 * k);
+      zc[lane] = w;  // placement cursors
+    }
+    __syncwarp();
+    if (bq0 >= 0) sm.zidx[(atomicAdd(&zc[bq0 >> 2], 1u << (8 * (bq0 & 3))) >> (8 * (bq0 & 3))) & 255u] =
+        (uint8_t)(l1b + lane);
+    if (bq1 >= 0) sm.zidx[(atomicAdd(&zc[bq1 >> 2], 1u << (8 * (bq1 & 3))) >> (8 * (bq1 & 3))) & 255u] =
+        (uint8_t)(l1b + lane + 32);
+    __syncwarp();
+  }
+  for (int j0 = 0; j0 < n1 && !over; j0 += 32) {
+    const int j = j0 + lane;
+    const bool has = j < n1;
+    const int i1 = l1a + j;
+    float x1 = 0.f, y1 = 0.f, z1 = 0.f;
+    int n0w = 0, a0 = 0, n0a = 0, n2w = 0;
+    if (has) {
+      x1 = sm.x[i1];
+      y1 = sm.y[i1];
+      z1 = sm.z[i1];
+      const int b1 = layer1_bin(sm.bstart, i1);
+      const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
+      a0 = sm.bstart[s0];
+      n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
+      n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
+      if (stats) {
+        const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
+        n2w = sm.bstart[2 * NB + min(s2 + nb2, NB)] - sm.bstart[2 * NB + s2] +
+              (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - sm.bstart[2 * NB] : 0);
+      }
+    }
+    npair += n0w + n2w;
+    // 1. Phi01 partners into regions of p01
+    int e0 = n0w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, e0, o);
+      if (lane >= o) e0 += t;
+    }
+    const int r0 = e0 - n0w;
+    if (__shfl_sync(FULL, e0, 31) > W_P01) {
+      over = true;
+      break;
+    }
+    int c01 = 0;
+    for (int k = 0; k < n0w; ++k) {
+      const int i0 = k < n0a ? a0 + k : k - n0a;
+      if (phi_pass(sm.x[i0], sm.y[i0], x1, y1, C.c01)) sm.p01[r0 + c01++] = (uint8_t)i0;
+    }
+    // 2. Phi12 partners: bit q of (mlo, mhi) for z-ordered layer-2 hit q
+    uint32_t mlo = 0u, mhi = 0u;
+    for (int q = 0; q < n2; ++q) {
+      const int i2 = sm.zidx[q];
+      const uint32_t pp = phi_pass(x1, y1, sm.x[i2], sm.y[i2], C.c12) ? 1u : 0u;
+      if (q < 32) mlo |= pp << q;
+      else mhi |= pp << (q - 32);
+    }
+    const int c12all = __popc(mlo) + __popc(mhi);
+    ntt += (unsigned)(c01 * c12all);
+    // 3. pairs whose layer-1 hit has Phi12 partners
+    const int pc = c12all ? c01 : 0;
+    int pe = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, pe, o);
+      if (lane >= o) pe += t;
+    }
+    const int pre = pe - pc;
+    const int T = __shfl_sync(FULL, pe, 31);
+    for (int k0 = 0; k0 < T; k0 += 32) {
+      const int k = k0 + lane;
+      int ow = 0;  // the last lane whose pairs start at or before k
+#pragma unroll
+      for (int st = 16; st; st >>= 1) {
+        const int pv = __shfl_sync(FULL, pre, ow + st);
+        if (pv <= k) ow += st;
+      }
+      const int pre_o = __shfl_sync(FULL, pre, ow), r0_o = __shfl_sync(FULL, r0, ow);
+      const float px1 = __shfl_sync(FULL, x1, ow), py1 = __shfl_sync(FULL, y1, ow), pz1 = __shfl_sync(FULL, z1, ow);
+      const uint32_t pml = __shfl_sync(FULL, mlo, ow), pmh = __shfl_sync(FULL, mhi, ow);
+      int i0 = 0;
+      float tl01 = 0.f;
+      unsigned long long cm = 0ull;
+      if (k < T) {
+        i0 = sm.p01[r0_o + (k - pre_o)];
+        tl01 = tan_l01(sm.z[i0], pz1, C);
+        const float zlo = pz1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
+        const float zhi = pz1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
+        const int lo = sm.zbs[zbin2(zlo, C)], hi = sm.zbs[zbin2(zhi, C) + 1];
+        const unsigned long long below_hi = hi >= 64 ? ~0ull : (1ull << hi) - 1ull;
+        const unsigned long long below_lo = lo >= 64 ? ~0ull : (1ull << lo) - 1ull;
+        cm = (below_hi & ~below_lo) & (((unsigned long long)pmh << 32) | pml);
+      }
+      const int cnt = __popcll(cm);
+      int ce = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, ce, o);
+        if (lane >= o) ce += t;
+      }
+      const int cpre = ce - cnt, ctot = __shfl_sync(FULL, ce, 31);
+      for (int c0 = 0; c0 < ctot; c0 += W_CAND) {
+        // each lane lists its candidates numbered c0 .. c0 + W_CAND - 1: pair lane, z-order position
+        unsigned long long m = cm;
+        for (int idx = cpre; m; ++idx) {
+          const int q = __ffsll((long long)m) - 1;
+          m &= m - 1ull;
+          if (idx >= c0 && idx < c0 + W_CAND) sm.cand[idx - c0] = (uint16_t)((lane << 6) | q);
+        }
+        __syncwarp();
+        const int ne = min(ctot - c0, W_CAND);
+        for (int e0 = 0; e0 < ne; e0 += 32) {
+          const int e = e0 + lane;
+          const int ent = e < ne ? sm.cand[e] : 0;
+          const int pl = ent >> 6;
+          const int ci0 = __shfl_sync(FULL, i0, pl), cow = __shfl_sync(FULL, ow, pl);
+          const float ctl = __shfl_sync(FULL, tl01, pl);
+          const float cx1 = __shfl_sync(FULL, px1, pl), cy1 = __shfl_sync(FULL, py1, pl),
+                      cz1 = __shfl_sync(FULL, pz1, pl);
+          bool pass = false;
+          int ci2 = 0;
+          if (e < ne) {
+            ci2 = sm.zidx[ent & 63];
+            const float x2 = sm.x[ci2], y2 = sm.y[ci2];
+            pass = dl_pass(cz1, sm.z[ci2], ctl, C) && rtc_pass(sm.x[ci0], sm.y[ci0], cx1, cy1, x2, y2, C);
+          }
+          const unsigned bm = __ballot_sync(FULL, pass);
+          const int kk = nt + __popc(bm & ((1u << lane) - 1u));
+          if (pass && kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(ci0, l1a + j0 + cow, ci2);
+          nt += __popc(bm);
+        }
+        __syncwarp();
+        if (nt > C.max_trip) break;  // the frame overflows: its decision is known
+      }
+      if (nt > C.max_trip) break;
+    }
+    if (nt > C.max_trip) break;
+  }
+  if (over) npair = ntt = 0;  // the frame is counted by the stage that takes it over
+  if (lane == 0) {
+    sm.ntrip = nt;
+    sm.bad = over ? 2 : 0;
+  }
+  __syncwarp();
+}
+
 constexpr int PENDING = -2;  // frame_front result: triplets selected, later stages to run
 
 // Stages A-C of one frame (load, sort, selection cuts).  Returns a final reason,
@@ -767,36 +1055,86 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
       for (int k = 0; k < ST_REASON0; ++k) sm.facc[k] = 0;
   }
   g.sync();
-  for (int i = g.rank(); i < n; i += G::N) {
-    const Dec d = decode(C, (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i)));
-    if (!d.ok) sm.bad = 1;
-    else if (n <= CH) bucket_add(sm, d.L * NB + d.b);
-  }
-  g.sync();
-  if (sm.bad) {
-    if (g.leader()) atomicOr(P.err, ERR_BADHIT);
-    return M3E_ERR_BADHIT;
-  }
-  if (n > C.max_hits || n > CH) return M3E_HIT_OVERFLOW;
-  if (stats && g.leader()) {
-    sm.facc[ST_FRAMES] += 1;
-    sm.facc[ST_HITS] += n;
-  }
+  if constexpr (G::N == 32 && DEFER) {
+    // warp stage (n <= CH): each lane holds its hits' addresses in registers, so the
+    // loads of a frame (addresses, then the table entries) are all in flight at once
+    constexpr int K = (CH + 31) / 32;
+    const int lane = g.rank();
+    uint32_t av[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = lane + 32 * k;
+      av[k] = i < n ? (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i)) : 0u;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (lane + 32 * k < n) {
+        const Dec d = decode(C, av[k]);
+        if (!d.ok) bad = true;
+        else bucket_add(sm, d.L * NB + d.b);
+      }
+    }
+    if (__any_sync(FULL, bad)) {
+      if (g.leader()) atomicOr(P.err, ERR_BADHIT);
+      return M3E_ERR_BADHIT;
+    }
+    if (n > C.max_hits) return M3E_HIT_OVERFLOW;
+    if (stats && g.leader()) {
+      sm.facc[ST_FRAMES] += 1;
+      sm.facc[ST_HITS] += n;
+    }
+    // ---- B: counting sort by (layer, phi bin); the table entries go straight from
+    // global to shared memory (asynchronous 4-byte copies, all of the lane's in flight)
+    bucket_scan(g, sm);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = lane + 32 * k;
+      if (i < n) {
+        const Dec d = decode(C, av[k]);
+        const int pos = bucket_add(sm, d.L * NB + d.b);
+        const float* cl = reinterpret_cast<const float*>(P.col_lut + C.col_off[d.L] + d.g);
+        cp_async4(&sm.x[pos], cl);
+        cp_async4(&sm.y[pos], cl + 1);
+        if constexpr (S::kPhi) cp_async4(&sm.phi[pos], cl + 2);
+        cp_async4(&sm.z[pos], P.row_lut + C.row_off[d.L] + d.row);
+        if constexpr (S::kAddr) sm.addr[pos] = av[k];
+        if constexpr (S::kIdx) sm.inidx[pos] = (uint16_t)i;
+      }
+    }
+    cp_async_wait_all();
+  } else {
+    for (int i = g.rank(); i < n; i += G::N) {
+      const Dec d = decode(C, (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i)));
+      if (!d.ok) sm.bad = 1;
+      else if (n <= CH) bucket_add(sm, d.L * NB + d.b);
+    }
+    g.sync();
+    if (sm.bad) {
+      if (g.leader()) atomicOr(P.err, ERR_BADHIT);
+      return M3E_ERR_BADHIT;
+    }
+    if (n > C.max_hits || n > CH) return M3E_HIT_OVERFLOW;
+    if (stats && g.leader()) {
+      sm.facc[ST_FRAMES] += 1;
+      sm.facc[ST_HITS] += n;
+    }
 
-  // ---- B: counting sort by (layer, phi bin)
-  bucket_scan(g, sm);
-  for (int i = g.rank(); i < n; i += G::N) {
-    const uint32_t a = (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i));
-    const Dec d = decode(C, a);
-    const int key = d.L * NB + d.b;
-    const int pos = bucket_add(sm, key);
-    const float4 cl = __ldg(P.col_lut + C.col_off[d.L] + d.g);
-    sm.x[pos] = cl.x;
-    sm.y[pos] = cl.y;
-    if constexpr (S::kPhi) sm.phi[pos] = cl.z;
-    sm.z[pos] = __ldg(P.row_lut + C.row_off[d.L] + d.row);
-    if constexpr (S::kAddr) sm.addr[pos] = a;
-    if constexpr (S::kIdx) sm.inidx[pos] = (uint16_t)i;
+    // ---- B: counting sort by (layer, phi bin)
+    bucket_scan(g, sm);
+    for (int i = g.rank(); i < n; i += G::N) {
+      const uint32_t a = (uint32_t)(LIVE ? __ldcv(hp + i) : __ldg(hp + i));
+      const Dec d = decode(C, a);
+      const int key = d.L * NB + d.b;
+      const int pos = bucket_add(sm, key);
+      const float4 c4 = __ldg(P.col_lut + C.col_off[d.L] + d.g);
+      sm.x[pos] = c4.x;
+      sm.y[pos] = c4.y;
+      if constexpr (S::kPhi) sm.phi[pos] = c4.z;
+      sm.z[pos] = __ldg(P.row_lut + C.row_off[d.L] + d.row);
+      if constexpr (S::kAddr) sm.addr[pos] = a;
+      if constexpr (S::kIdx) sm.inidx[pos] = (uint16_t)i;
+    }
   }
   g.sync();
 
@@ -808,167 +1146,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     const int l1a = sm.bstart[NB], l1b = sm.bstart[2 * NB];
     const int nb0 = min(2 * C.k01 + 1, NB), nb2 = min(2 * C.k12 + 1, NB);
     if constexpr (G::N == 32) {
-      // Warp: the work is flattened so that every lane has a candidate at every
-      // step.  A: one lane per layer-1 hit collects its Phi01 and Phi12 partners
-      // into regions reserved by a prefix sum of the window sizes.  B: a prefix sum
-      // of the products c01 * c12 numbers the candidate triplets of all layer-1
-      // hits.  C: the lanes share that flat list (a binary search finds the
-      // layer-1 hit of a candidate) for the Delta lambda and r_tc tests.
-      const int lane = g.rank();
-      const int n1 = l1b - l1a;
-      int base0 = 0, base2 = 0, basec = 0;
-      bool over = false;
-      for (int j0 = 0; j0 < n1; j0 += 32) {
-        const int j = j0 + lane;
-        const int i1 = l1a + j;
-        int n0w = 0, n2w = 0, a0 = 0, n0a = 0, a2 = 0, n2a = 0;
-        float x1 = 0.f, y1 = 0.f;
-        if (j < n1) {
-          x1 = sm.x[i1];
-          y1 = sm.y[i1];
-          const int b1 = layer1_bin(sm.bstart, i1);
-          const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
-          const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
-          a0 = sm.bstart[s0];
-          n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
-          n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
-          a2 = sm.bstart[2 * NB + s2];
-          n2a = sm.bstart[2 * NB + min(s2 + nb2, NB)] - a2;
-          n2w = n2a + (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - sm.bstart[2 * NB] : 0);
-        }
-        npair += n0w + n2w;
-        // exclusive prefix of the window sizes: each layer-1 hit's region of partners
-        int e0 = n0w, e2 = n2w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t0 = __shfl_up_sync(FULL, e0, o), t2 = __shfl_up_sync(FULL, e2, o);
-          if (lane >= o) {
-            e0 += t0;
-            e2 += t2;
-          }
-        }
-        const int r0 = base0 + e0 - n0w, r2 = base2 + e2 - n2w;
-        base0 += __shfl_sync(FULL, e0, 31);
-        base2 += __shfl_sync(FULL, e2, 31);
-        over = over || base0 > W_P01 || base2 > W_P12;
-        int c01 = 0, c12 = 0, c12all = 0;
-        if (j < n1 && !over) {
-          const float z1 = sm.z[i1];
-          float tlmin = FLT_MAX, tlmax = -FLT_MAX;
-          for (int k = 0; k < n0w; ++k) {
-            const int i0 = k < n0a ? a0 + k : k - n0a;
-            if (sm.x[i0] * x1 + sm.y[i0] * y1 >= C.c01) {
-              sm.p01[r0 + c01++] = (uint8_t)i0;
-              const float tl = (z1 - sm.z[i0]) * C.inv_dr01;
-              tlmin = fminf(tlmin, tl);
-              tlmax = fmaxf(tlmax, tl);
-            }
-          }
-          if (c01) {
-            // a Phi12 partner is stored only inside the union of its pairs' z windows
-            // (part C), spanned by the smallest and largest tan(lambda01) of the
-            // Phi01 partners; c12all counts them all for the statistics
-            const float zlo = z1 + (tlmin - C.dl_max) * C.dr12 - 1e-3f;
-            const float zhi = z1 + (tlmax + C.dl_max) * C.dr12 + 1e-3f;
-            for (int k = 0; k < n2w; ++k) {
-              const int i2 = k < n2a ? a2 + k : sm.bstart[2 * NB] + (k - n2a);
-              if (x1 * sm.x[i2] + y1 * sm.y[i2] >= C.c12) {
-                ++c12all;
-                const float z2 = sm.z[i2];
-                if (z2 >= zlo && z2 <= zhi) sm.p12[r2 + c12++] = (uint8_t)i2;
-              }
-            }
-          }
-          sm.r01[j] = (uint16_t)r0;
-          sm.r12[j] = (uint16_t)r2;
-          sm.c12[j] = (uint8_t)c12;
-        }
-        // B: exclusive prefix of the (layer-1 hit, Phi01 partner) pairs that have
-        // Phi12 partners; ntt counts their candidate triplets
-        ntt += c01 * c12all;
-        const int pc = c12 ? c01 : 0;
-        int ec = pc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(FULL, ec, o);
-          if (lane >= o) ec += t;
-        }
-        if (j < n1) sm.cst[j] = (uint16_t)(basec + ec - pc);
-        basec += __shfl_sync(FULL, ec, 31);
-      }
-      if (lane == 0) sm.cst[n1] = (uint16_t)basec;
-      sm.bad = __any_sync(FULL, over) ? 2 : 0;
-      __syncwarp();
-      if (sm.bad == 2) {
-        npair = ntt = 0;  // the frame is counted by the stage that takes it over
-      } else {
-        // C: one lane per (layer-1 hit, Phi01 partner) pair; the lanes walk their
-        // Phi12 partners in lock step.  A z window on the layer-2 hit (the Delta
-        // lambda cut as seen from the pair, widened by 1e-3 mm against rounding)
-        // skips most partners before the exact Delta lambda and r_tc tests, which
-        // are the same expressions as in the CTA stage.
-        int nt = 0;
-        const int T = basec;
-        int jc = 0;  // layer-1 hit of the first pair of the round
-        for (int k0 = 0; k0 < T; k0 += 32) {
-          const int k = k0 + lane;
-          const int kend = min(k0 + 32, T);
-          // the owners of the round's pairs: lane t writes those of layer-1 hit jb + t
-          for (int jb = jc; jb < n1 && sm.cst[jb] < kend; jb += 32) {
-            const int jt = jb + lane;
-            if (jt < n1) {
-              const int e = min(sm.cst[jt + 1], kend);
-              for (int q = max(sm.cst[jt], k0); q < e; ++q) sm.own[q - k0] = (uint8_t)jt;
-            }
-          }
-          __syncwarp();
-          const int j = k < T ? sm.own[lane] : 0;
-          jc = sm.own[kend - 1 - k0];
-          __syncwarp();
-          int i0 = 0, i1 = 0, r2 = 0, c2 = 0;
-          float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f, tl01 = 0.f, zlo = 0.f, zhi = -1.f;
-          if (k < T) {
-            i1 = l1a + j;
-            i0 = sm.p01[sm.r01[j] + (k - sm.cst[j])];
-            r2 = sm.r12[j];
-            c2 = sm.c12[j];
-            x0 = sm.x[i0];
-            y0 = sm.y[i0];
-            x1 = sm.x[i1];
-            y1 = sm.y[i1];
-            z1 = sm.z[i1];
-            tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
-            zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
-            zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
-          }
-          const int cmax = (int)__reduce_max_sync(FULL, (unsigned)c2);
-          for (int b = 0; b < cmax; ++b) {
-            bool pass = false;
-            int i2 = 0;
-            if (b < c2) {
-              i2 = sm.p12[r2 + b];
-              const float z2 = sm.z[i2];
-              if (z2 >= zlo && z2 <= zhi && fabsf(fmaf(z2 - z1, C.inv_dr12, -tl01)) <= C.dl_max) {
-                const float x2 = sm.x[i2], y2 = sm.y[i2];
-                const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
-                const float cr = ax * by - ay * bx;
-                const float ex = x2 - x0, ey = y2 - y0;
-                const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
-                const float Qq = cr * cr;
-                pass = cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq;
-              }
-            }
-            const unsigned m = __ballot_sync(FULL, pass);
-            const int kk = nt + __popc(m & ((1u << lane) - 1u));
-            if (pass && kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
-            nt += __popc(m);
-            if (nt > C.max_trip) break;  // the frame overflows: its decision is known
-          }
-          if (nt > C.max_trip) break;
-        }
-        if (lane == 0) sm.ntrip = nt;
-        // npair and ntt are each lane's share (its layer-1 hits): all lanes add them
-      }
+      warp_cuts<S, CT>(sm, C, stats, npair, ntt);
     } else {
       // CTA stage: a warp per layer-1 hit.  The Phi01 window is walked in warp-uniform
       // steps; for each Phi01 partner the lanes split the Phi12 window, a z window
@@ -998,7 +1176,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
         if (stats) {
           for (int k = lane; k < n2w; k += 32) {
             const int i2 = k < n2a ? a2 + k : w2 + (k - n2a);
-            c12 += x1 * sm.x[i2] + y1 * sm.y[i2] >= C.c12;
+            c12 += phi_pass(x1, y1, sm.x[i2], sm.y[i2], C.c12);
           }
           c12 = (int)__reduce_add_sync(FULL, (unsigned)c12);
         }
@@ -1009,7 +1187,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
           bool p01 = false;
           if (kb + lane < n0w) {
             i0l = kb + lane < n0a ? a0 + kb + lane : kb + lane - n0a;
-            p01 = sm.x[i0l] * x1 + sm.y[i0l] * y1 >= C.c01;
+            p01 = phi_pass(sm.x[i0l], sm.y[i0l], x1, y1, C.c01);
           }
           unsigned mp = __ballot_sync(FULL, p01);
           if (lane == 0) ntt += __popc(mp) * c12;
@@ -1018,7 +1196,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
             const int i0 = __shfl_sync(FULL, i0l, __ffs(mp) - 1);
             mp &= mp - 1;
             const float x0 = sm.x[i0], y0 = sm.y[i0];
-            const float tl01 = (z1 - sm.z[i0]) * C.inv_dr01;
+            const float tl01 = tan_l01(sm.z[i0], z1, C);
             const float zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
             const float zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
             for (int k = lane; k < n2w; k += 32) {
@@ -1026,14 +1204,9 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
               const float z2 = sm.z[i2];
               if (!(z2 >= zlo && z2 <= zhi)) continue;
               const float x2 = sm.x[i2], y2 = sm.y[i2];
-              if (!(x1 * x2 + y1 * y2 >= C.c12)) continue;
-              if (!(fabsf(fmaf(z2 - z1, C.inv_dr12, -tl01)) <= C.dl_max)) continue;
-              const float ax = x0 - x1, ay = y0 - y1, bx = x2 - x1, by = y2 - y1;
-              const float cr = ax * by - ay * bx;
-              const float ex = x2 - x0, ey = y2 - y0;
-              const float Pq = (ax * ax + ay * ay) * (bx * bx + by * by) * (ex * ex + ey * ey);
-              const float Qq = cr * cr;
-              if (!(cr != 0.f && Pq >= C.rtc_lo2 * Qq && Pq <= C.rtc_hi2 * Qq)) continue;
+              if (!phi_pass(x1, y1, x2, y2, C.c12)) continue;
+              if (!dl_pass(z1, z2, tl01, C)) continue;
+              if (!rtc_pass(x0, y0, x1, y1, x2, y2, C)) continue;
               const int kk = atomicAdd(&sm.ntrip, 1);
               if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
             }
@@ -1168,6 +1341,14 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
         P.dump.combo_val[4 * r + 1] = v.chi2;
         P.dump.combo_val[4 * r + 2] = v.tdist;
         P.dump.combo_val[4 * r + 3] = v.ptot;
+        if (P.dump.combo_aux) {
+          float dm, fm;
+          vertex_soft(load_track(sm.t, a), load_track(sm.t, b), load_track(sm.t, e), C.isect_lim, dm, fm);
+          P.dump.combo_aux[4 * r + 0] = dm;
+          P.dump.combo_aux[4 * r + 1] = fm;
+          P.dump.combo_aux[4 * r + 2] = v.chi2_second;
+          P.dump.combo_aux[4 * r + 3] = 0.f;
+        }
       }
     }
     found = g.any(pass) || found;

@@ -16,7 +16,9 @@ constexpr int DEFERRED = -1;      // process_frame result: frame too large for t
 // typical frames; anything above its capacities is re-run by the CTA stage,
 // whose capacities are the configuration limits.
 constexpr int W_HITS = 160, W_TRIP = 160, W_TRK = 48, W_COMBO = 512;
-constexpr int W_P01 = 384, W_P12 = 1024;  // warp stage: Phi-cut partner lists
+constexpr int W_P01 = 384;        // warp stage: Phi01 partners of 32 layer-1 hits
+constexpr int W_L2 = 64;          // warp stage: layer-2 hits (bit masks of two words)
+constexpr int W_CAND = 256;       // warp stage: candidate triplets written per step
 constexpr int C_HITS = 4096, C_TRIP = 1024, C_TRK = 128, C_COMBO = 1024;
 constexpr int WARPS_PER_CTA = 4;  // persistent warp kernel: warps (frames in flight) per CTA
 constexpr int CTA_THREADS = 256;  // large-frame kernel
@@ -27,12 +29,14 @@ struct DevCfg {
   float r[4];
   float inv_dr01, inv_dr12;   // 1/(r1 - r0), 1/(r2 - r1), nominal radii
   float dr12;                 // r2 - r1
+  float zoff2, izw2;          // layer-2 z bin of the warp stage: (z + zoff2) * izw2, NB bins over the length
   float c01, c12;             // cos(phi_max) * r_i * r_j: a pair passes when h_i . h_j >= c
   float dl_max;               // |Delta lambda| <= dl_max
   float rtc_lo2, rtc_hi2;     // (2 rtc_min)^2, (2 rtc_max)^2 against (d01 d12 d20)^2 / cross^2
   int k01, k12;               // phi-bin half windows of the two pair cuts
   int ntot[4], ncol[4], nlad[4], nrow[4];
   float intot[4];             // 1 / ntot, rounded once (phi bin of a column, decode)
+  float phs_hi[4], phs_lo[4]; // 2 pi / ntot as a sum of two floats (phi of a column by exact FP32 steps)
   int col_off[4], row_off[4]; // offsets of each layer in the look-up tables
   float kB;                   // p [MeV] = kB * R [mm]
   float hl[4];                // Highland width numerator: sigma_MS(p) = hl[layer] / p
@@ -109,6 +113,11 @@ int fused_blocks_per_sm();
 int stage_blocks_per_sm(int stage);
 size_t fused_smem_bytes();
 size_t cta_smem_bytes();
+
+// Hit ingest (m3e_ingest.cu): addresses -> FP32 x, y, z (and phi unless null) as SoA.
+int ingest_blocks_per_sm();
+cudaError_t launch_ingest(const DevCfg& c, const int32_t* hits, int64_t n, const float4* col_lut, const float* row_lut,
+                          float* x, float* y, float* z, float* phi, int* err, int grid, cudaStream_t s);
 
 // Gradient of the fit chi2 (m3e_grad.cu).
 int fit_grad_blocks(int sms, int64_t n_cand);

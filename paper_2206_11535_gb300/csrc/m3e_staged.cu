@@ -18,8 +18,8 @@ namespace {
 
 constexpr int NL3 = NB + 1;                        // layer-3 bin starts per frame
 constexpr int S1_TRIP = 160;                       // stage-1 warp-tier triplet capacity
-// phi re-read at emit; input indices instead of addresses (emit re-reads the few it needs)
-using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1, false, true, false>;
+// phi and the address of each hit at hand for the emit (no global re-reads)
+using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1>;
 using SmFrontD = FrameSm<W_HITS, S1_TRIP, 1, 1>;                // candidate record: with input indices
 constexpr int M_HITS = 1024;                       // stage-1 middle tier (CTA per frame)
 using SmFrontMid = FrameSm<M_HITS, C_TRIP, 1, 1>;
@@ -453,7 +453,9 @@ __device__ __forceinline__ void load_circle(const float4* __restrict__ rec, int6
 
 template <bool DEBUG>
 __device__ __forceinline__ void stage4_dump(const DevCfg& C, const KParams& P, const SParams& S, int64_t i,
-                                            const int4& r, const VtxOut& v, float esum) {
+                                            const int4& r, const VtxOut& v, const TrackR& A, const TrackR& B,
+                                            const TrackR& E) {
+  const float esum = A.E + B.E + E.E;
   const int f = r.x;
   const int c = (int)(i - S.fcbase[f]);
   if (c < P.dump.cap_combo) {
@@ -467,6 +469,14 @@ __device__ __forceinline__ void stage4_dump(const DevCfg& C, const KParams& P, c
     P.dump.combo_val[4 * d + 1] = v.chi2;
     P.dump.combo_val[4 * d + 2] = v.tdist;
     P.dump.combo_val[4 * d + 3] = v.ptot;
+    if (P.dump.combo_aux) {
+      float dm, fm;
+      vertex_soft(A, B, E, C.isect_lim, dm, fm);
+      P.dump.combo_aux[4 * d + 0] = dm;
+      P.dump.combo_aux[4 * d + 1] = fm;
+      P.dump.combo_aux[4 * d + 2] = v.chi2_second;
+      P.dump.combo_aux[4 * d + 3] = 0.f;
+    }
   }
 }
 
@@ -495,14 +505,9 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
           load_circle(S.trec, r.w, ce[0], ce[1], ce[2]);
           const int st = vertex_prefilter(ca, cb, ce, C.isect_lim);
           cand = st == 2;
-          if (DEBUG && !cand) {  // record the combination with its early status
-            VtxOut v;
-            v.status = st;
-            v.pass = 0;
-            v.chi2 = v.tdist = v.ptot = FLT_MAX;
-            const float4 qa = __ldg(S.trec + 4 * (int64_t)r.y + 1), qb = __ldg(S.trec + 4 * (int64_t)r.z + 1),
-                         qe = __ldg(S.trec + 4 * (int64_t)r.w + 1);
-            stage4_dump<DEBUG>(C, P, S, i, r, v, qa.w + qb.w + qe.w);
+          if (DEBUG && !cand) {  // record the combination with its early status (the same geometry)
+            const TrackR A = load_track(S.trec, r.y), B = load_track(S.trec, r.z), E = load_track(S.trec, r.w);
+            stage4_dump<DEBUG>(C, P, S, i, r, vertex(A, B, E, C), A, B, E);
           }
         }
       }
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
         if (P.stats && v.status == 2)
           nvo += !pz_fails_ptot(pz_sum(pz_track(A.p, A.ct), pz_track(B.p, B.ct), pz_track(E.p, E.ct)), C.ptot_max);
         if (v.pass) S.ffound[r.x] = 1;
-        if (DEBUG) stage4_dump<DEBUG>(C, P, S, i, r, v, A.E + B.E + E.E);
+        if (DEBUG) stage4_dump<DEBUG>(C, P, S, i, r, v, A, B, E);
       }
       qn -= take;
       __syncwarp();

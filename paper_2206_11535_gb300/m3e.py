@@ -52,7 +52,8 @@ N_STATS = len(STATS_FIELDS) + 8
 class Dump(C.Structure):
     _fields_ = [("cap_trip", C.c_int32), ("cap_combo", C.c_int32),
                 ("n_trip", C.c_void_p), ("trip", C.c_void_p), ("trk_status", C.c_void_p), ("trk_val", C.c_void_p),
-                ("n_combo", C.c_void_p), ("combo", C.c_void_p), ("combo_val", C.c_void_p)]
+                ("n_combo", C.c_void_p), ("combo", C.c_void_p), ("combo_val", C.c_void_p),
+                ("combo_aux", C.c_void_p)]
 
 
 class Tuning(C.Structure):
@@ -103,6 +104,7 @@ def _load(path: str = LIB_PATH):
     lib.m3e_autotune.argtypes = [vp, vp, vp, i64, vp, vp, C.POINTER(Tuning)]
     lib.m3e_select_frames_host.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.m3e_select_frames_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    lib.m3e_ingest.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
     lib.m3e_check.argtypes = [vp, vp]
     lib.m3e_set_launch.argtypes = [vp, C.c_int, C.c_int]
     lib.m3e_set_host_pipeline.argtypes = [vp, C.c_int, C.c_int, C.c_int]
@@ -250,9 +252,10 @@ class Context:
                    trk_val=torch.zeros((nf, cap_trip, 4), dtype=torch.float32, device=dev),
                    n_combo=torch.zeros(nf, dtype=torch.int32, device=dev),
                    combo=torch.full((nf, cap_combo, 4), -2, dtype=torch.int32, device=dev),
-                   combo_val=torch.zeros((nf, cap_combo, 4), dtype=torch.float32, device=dev))
+                   combo_val=torch.zeros((nf, cap_combo, 4), dtype=torch.float32, device=dev),
+                   combo_aux=torch.zeros((nf, cap_combo, 4), dtype=torch.float32, device=dev))
         d = Dump(cap_trip, cap_combo, *[_ptr(rec[k]) for k in ("n_trip", "trip", "trk_status", "trk_val", "n_combo",
-                                                                  "combo", "combo_val")])
+                                                                  "combo", "combo_val", "combo_aux")])
         _check(lib.m3e_select_frames_debug(self._h, form, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
                                            C.byref(d), _stream(stream)))
         rec["keep"], rec["reason"] = keep, reason
@@ -267,6 +270,17 @@ class Context:
         _check(lib.m3e_select_frames_noalloc(self._h, _ptr(hits), _ptr(off), nf, _ptr(keep), _ptr(reason),
                                              _stream(stream)))
         return keep, reason
+
+    def ingest(self, hits, x=None, y=None, z=None, phi=None, with_phi: bool = True, stream=None):
+        """``m3e_ingest``: FP32 x, y, z (and phi) of every hit of the int32 device tensor
+        ``hits``, as four float32 device tensors (phi is None when not requested)."""
+        import torch
+        n = hits.numel()
+        mk = lambda t: torch.empty(n, dtype=torch.float32, device=hits.device) if t is None else t  # noqa: E731
+        x, y, z = mk(x), mk(y), mk(z)
+        phi = mk(phi) if with_phi else None
+        _check(lib.m3e_ingest(self._h, _ptr(hits), n, _ptr(x), _ptr(y), _ptr(z), _ptr(phi), _stream(stream)))
+        return x, y, z, phi
 
     def set_host_pipeline(self, max_chunks: int = 16, wait_ms: int = 2000, drop_chunk: int = -1):
         """``m3e_set_host_pipeline``: chunking and the bounded chunk wait of

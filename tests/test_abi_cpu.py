@@ -79,7 +79,8 @@ def _c_layout(struct: str, fields: list[str], tmp_path) -> list[int]:
 
 @pytest.mark.parametrize("name,struct", [("Result", "m3e_result"), ("StreamParams", "m3e_stream_params"),
                                          ("StreamStatus", "m3e_stream_status"), ("ReplayStats", "m3e_replay_stats"),
-                                         ("Tuning", "m3e_tuning"), ("Config", "m3e_config")])
+                                         ("Tuning", "m3e_tuning"), ("Config", "m3e_config"),
+                                         ("Dump", "m3e_dump")])
 def test_ctypes_mirrors_match_the_c_layout(name, struct, tmp_path):
     import shutil
     if not shutil.which("gcc") or not os.path.exists("/usr/local/cuda/include/cuda_runtime.h"):

@@ -37,6 +37,7 @@ def _np(rec):
 
 def _check_results(res, max_boundary_frac=0.01):
     s = P.summary(res)
+    print("boundary differences per band", {k: v for k, v in P.band_counts(res).items() if v})
     fails = [r for r in res if r.status == "fail"]
     msg = "\n".join(f"frame {r.frame}: {r.fails[:4]}" for r in fails[:10])
     assert s["fail"] == 0, f"{s}\n{msg}"
@@ -109,6 +110,26 @@ def gen_subbatch(d, frames):
     off = np.zeros(len(frames) + 1, np.int64)
     off[1:] = np.cumsum([p.size for p in parts])
     return dict(hits=np.concatenate(parts) if parts else np.zeros(0, np.int32), off=off)
+
+
+def test_derived_errors_leave_margin(ctx, ocfg):
+    """The bands of the derived variables hold at least twice the largest difference
+    measured here between the CUDA path and the oracle on matched candidates (all
+    parity frames and 2,000 throughput frames, every form)."""
+    worst = {}
+    for wl, n in (("c1", None), ("c2", 2000)):
+        d = gen.workload(wl) if n is None else gen.workload(wl, n_frames=n)
+        for form in FORMS.values():
+            rec = _np(ctx.select_frames_debug(*_dev(d), cap_trip=1024, cap_combo=1024, form=form))
+            for k, (m, cnt) in P.matched_errors(ocfg, d["hits"], d["off"], rec).items():
+                worst[k] = max(worst.get(k, 0.0), m)
+    print("largest differences", {k: f"{v:.2e}" for k, v in worst.items()})
+    assert worst["kappa"] <= P.KAPPA_REL / 2 and worst["theta"] <= P.THETA_REL / 2
+    assert 2 * worst["fourth_hit"] <= P.BAND["fourth_hit"] / 2
+    for k in ("chi2_track", "energy", "vtx_chi2", "tdist", "ptot", "disc", "filter", "choice"):
+        assert worst[k] <= P.BAND[k] / 2, (k, worst[k], P.BAND[k])
+    for k in ("vtx_chi2", "tdist", "ptot"):
+        assert worst[k + "_value"] <= P.VAL_REL[k] / 2, (k, worst[k + "_value"])
 
 
 def test_permutation_invariance(ctx):
@@ -356,6 +377,36 @@ def test_graph_and_autotune_keep_decisions(m3e, cfg):
                 torch.cuda.synchronize()
                 assert (reason.cpu().numpy() == ref).all()
             g.close()
+        ctx.check()
+
+
+def test_graph_decisions_match_the_oracle(m3e, cfg, ocfg):
+    """The persistent batched form (autotuned, the batch captured as one CUDA graph)
+    against the FP64 oracle directly, on uneven frames: every frame's decision, and
+    for any frame that differs, a candidate-level check that the difference lies
+    inside a boundary band."""
+    d = gen.workload("c3", n_frames=3000, seed=33)
+    hits, off = _dev(d)
+    nf = d["off"].size - 1
+    _, o_reason = O.select_frames(ocfg, d["hits"], d["off"], 4)
+    with m3e.Context(cfg, 0) as ctx:
+        ctx.autotune(hits, off)
+        ctx.prepare(nf)
+        keep = torch.empty(nf, dtype=torch.uint8, device="cuda")
+        reason = torch.empty(nf, dtype=torch.uint8, device="cuda")
+        g = ctx.graph(hits, off, keep, reason, form=m3e.STAGED)
+        reason.fill_(9)
+        g.launch()
+        torch.cuda.synchronize()
+        r = reason.cpu().numpy()
+        g.close()
+        diff = np.nonzero(r != o_reason)[0]
+        for f in diff:
+            sub = gen_subbatch(d, [int(f)])
+            rec = _np(ctx.select_frames_debug(*_dev(sub), cap_trip=1024, cap_combo=1024))
+            res = P.compare_frame(ocfg, sub["hits"], P.record_of_frame(rec, 0), int(f))
+            assert res.status == "boundary", (int(f), res.fails[:3])
+        assert diff.size <= 0.01 * nf + 1
         ctx.check()
 
 

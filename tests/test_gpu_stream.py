@@ -7,7 +7,10 @@ import time
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2206_11535_gb300 import gen
+
+from . import parity as P
 
 pytestmark = pytest.mark.gpu
 
@@ -112,6 +115,42 @@ def test_stream_alone_and_in_the_mix(m3e, cfg):
         for f, (k, rs) in alone.items():
             assert (k, rs) == (rep["keep"][f], rep["reason"][f]) == (keep[f], reason[f]), f
         assert (rep["lat_submit_ns"] > 0).all() and (rep["lat_arrival_ns"] >= rep["lat_submit_ns"] - 1000).all()
+
+
+def _oracle_agrees(m3e, ctx, ocfg, hits, off, reason, form):
+    """Every frame's decision equals the FP64 oracle's, except frames whose differences
+    all lie inside a boundary band (candidate by candidate, with the record of `form`)."""
+    _, o_reason = O.select_frames(ocfg, hits, off, 4)
+    diff = np.nonzero(o_reason != reason)[0]
+    for f in diff:
+        sub = np.ascontiguousarray(hits[off[f]:off[f + 1]])
+        so = np.array([0, sub.size], np.int64)
+        rec = ctx.select_frames_debug(torch.from_numpy(sub).cuda(), torch.from_numpy(so).cuda(), cap_trip=1024,
+                                      cap_combo=1024, form=form)
+        rec = {k: v.cpu().numpy() for k, v in rec.items()}
+        try:
+            ctx.check()
+        except m3e.M3EError:
+            pass
+        res = P.compare_frame(ocfg, sub, P.record_of_frame(rec, 0), int(f))
+        assert res.status == "boundary", (int(f), res.fails[:3])
+    assert diff.size <= 0.01 * reason.size + 1, diff.size
+    return diff.size
+
+
+def test_stream_decisions_match_the_oracle(m3e, cfg, ocfg):
+    """The streaming kernel's decisions against the FP64 oracle directly (not against
+    the library's batch path): 2,000 frames of the streaming mix with its special
+    frames (empty, heavy frames for the CTA kernel, more than max_hits, an invalid
+    address), replayed as Poisson arrivals."""
+    hits, off = _mixed_batch(cfg, n=2000)
+    with m3e.Context(cfg, 0) as ctx:
+        ctx.stream_open()
+        rep = ctx.stream_replay(hits, off, rate_hz=2.0e6, seed=17)
+        assert ctx.stream_close() == m3e.OK
+        nb = _oracle_agrees(m3e, ctx, ocfg, hits, off, rep["reason"], m3e.FUSED)
+        print("stream vs oracle: boundary frames", nb)
+        assert (rep["keep"] == (rep["reason"] != 0)).all()
 
 
 def test_stream_idle_exit_and_relaunch(m3e, cfg):

@@ -33,6 +33,7 @@ def test_decode_roundtrip_and_radius(cfg, ocfg):
             ntot = g["n_ladders"][L] * g["n_cols"][L]
             phi = (l_ * g["n_cols"][L] + c_ + 0.5) * 2 * math.pi / ntot
             assert abs(math.atan2(h.y, h.x) % (2 * math.pi) - phi) < 1e-12
+            assert abs(h.phi - phi) < 1e-13 and 0.0 <= h.phi < 2 * math.pi
             assert abs(h.z - (-g["half_len_mm"][L] + (r_ + 0.5) * g["pitch_mm"])) < 1e-12
 
 
