@@ -136,23 +136,27 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the sources the stage kernels compile from: their unit, the shared
-    device code and the parameter structs of the internal header (not its host
-    declarations)."""
+def kernel_source_hash(unit: str = "m3e_staged.cu") -> str:
+    """Hash of the sources a unit's kernels compile from: the unit, the shared device
+    code and the parameter structs of the internal header (not its host declarations)."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2206_11535_gb300", "csrc")
-    for f in ("m3e_staged.cu", "m3e_device.cuh"):
+    for f in (unit, "m3e_device.cuh"):
         h.update(open(os.path.join(src, f), "rb").read())
     txt = open(os.path.join(src, "m3e_internal.cuh"), "rb").read()
     h.update(txt[txt.index(b"constexpr int NB"):txt.index(b"// Host-side launchers")])
     return h.hexdigest()[:16]
 
 
+PROFILE_OF = {"ingest": ("ingest_c2_traffic.txt", "m3e_ingest.cu")}
+
+
 def _recorded(key: str):
-    """A per-frame counter of the committed ncu summary of the stage kernels, or None
-    when the summary was taken on other kernel sources (or lacks the key)."""
-    p = os.path.join(ROOT, "profiles", "staged_c2_traffic.txt")
+    """A counter of a committed ncu summary (the stage kernels', or the ingest kernel's
+    for keys ending in .ingest), or None when the summary was taken on other kernel
+    sources (or lacks the key)."""
+    fname, unit = PROFILE_OF.get(key.rsplit(".", 1)[-1], ("staged_c2_traffic.txt", "m3e_staged.cu"))
+    p = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(p):
         return None
     kv = {}
@@ -160,7 +164,7 @@ def _recorded(key: str):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+    if kv.get("kernel_source_sha256_16") != kernel_source_hash(unit):
         return None
     try:
         return float(kv[key])
@@ -195,6 +199,55 @@ def cpu_baseline(d, seconds_target=12.0):
     return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": f"first {n} frames of the rank-0 batch, FP64 C oracle (-O2), {cores} threads over "
                       f"disjoint frame ranges, brute force over every hit triplet ({dt:.1f} s)"}
+
+
+def measured_hbm_peak():
+    """(GB/s, source) of the machine's measured copy bandwidth, else the stated fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def ingest_roofline(ctx, hits, dev, stream, steps=20) -> dict:
+    """m3e_ingest over the whole batch's hits (int32 addresses -> x, y, z, phi as FP32
+    structure of arrays): 4 bytes read and 16 written per hit, against HBM."""
+    import torch
+    n = hits.numel()
+    outs = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(4)]
+    for _ in range(3):
+        ctx.ingest(hits, *outs, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.ingest(hits, *outs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.check()
+    peak, src = measured_hbm_peak()
+    alg = 20 * n
+    tr = _recorded("dram_bytes_per_hit.ingest")
+    del outs
+    return {"kernel": "k_ingest (m3e_ingest)", "bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
+            "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": src, "kernel_ms": ms,
+            "algorithmic_bytes": alg, "hits": n, "traffic": None if tr is None else tr * n}
+
+
+def compaction_roofline(nf: int, stage1_ms: float) -> dict | None:
+    """The stream-compaction writes of stage 1 (the sorted hits and the ballot-compacted
+    triplets of every frame it emits): DRAM bytes written per frame from the committed
+    ncu summary of the stage kernels, over this run's stage-1 time."""
+    wb = _recorded("dram_write_bytes_per_frame.stage1")
+    if wb is None or stage1_ms <= 0:
+        return None
+    peak, src = measured_hbm_peak()
+    gbs = wb * nf / (stage1_ms / 1e3) / 1e9
+    return {"kernel": "k_stage1 (emit of sorted hits and compacted triplets)", "bound": "alu (reported against hbm)",
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_source": src,
+            "dram_write_bytes_per_frame": wb}
 
 
 def parity_sample(ctx, d, dev, n_frames=2000):
@@ -343,7 +396,58 @@ def align_arm(ctx, gen, m3e, n_frames: int, dev, steps: int = 200) -> dict:
             "stiff_residual_over_injected": float(np.linalg.norm(res_m[stiff]) / np.linalg.norm(tru_m[stiff])),
             "weak_residual_over_injected": float(np.linalg.norm(res_m[~stiff]) / max(np.linalg.norm(tru_m[~stiff]),
                                                                                         1e-30)),
-            "modes": modes}
+            "modes": modes,
+            "field_scale": field_scale_fit(ctx, d, cand, hits, off, est, truth, dev)}
+
+
+def field_scale_fit(ctx, d, cand, hits, off, est, truth, dev) -> dict:
+    """The field scale, which the chi2 sum cannot fix (it grows as the square of the
+    scale), from the energy sum of the signal decays (Sec. "Vertex Fit": the three
+    tracks of mu+ -> e+ e- e+ at rest carry E = m_mu): the decays whose three tracks
+    the selection kept (each a truth-matched candidate), their curvatures from
+    m3e_fit_kappa at the fitted alignment, and the scale s that minimises
+    sum_decays (sum_i sqrt((k B s / |kappa_i|)^2 + m_e^2) - m_mu)^2 (Newton steps in FP64)."""
+    import torch
+    from paper_2206_11535_gb300 import gen as G
+    cfg = G.load_config()
+    kB = cfg["constants"]["k_MeV_per_T_mm"] * cfg["field"]["B_T"]
+    me, mmu = cfg["constants"]["m_e_MeV"], cfg["constants"]["m_mu_MeV"]
+    trk = d["hit_track"][cand]
+    tm = (trk[:, 0] >= 0) & (trk == trk[:, :1]).all(1)
+    first = {}
+    for k in np.nonzero(tm)[0]:
+        first.setdefault(int(trk[k, 0]), k)
+    sig = np.nonzero(d["trk_signal"])[0]
+    groups = {}
+    for t in sig:
+        groups.setdefault(int(d["trk_frame"][t]), []).append(int(t))
+    decays = np.array([[first[t] for t in g] for g in groups.values() if len(g) == 3 and all(t in first for t in g)],
+                      np.int64).reshape(-1, 3)
+    if decays.shape[0] == 0:
+        return {"signal_decays": 0}
+    sub = torch.from_numpy(np.ascontiguousarray(cand[decays.reshape(-1)])).to(dev)
+
+    def solve(params):
+        k = ctx.fit_kappa(hits, off, sub, torch.tensor(params, dtype=torch.float32, device=dev)).cpu().numpy()
+        p1 = (kB / np.abs(k.astype(np.float64))).reshape(-1, 3)
+        ok = np.isfinite(p1).all(1)
+        p1 = p1[ok]
+        s = 1.0
+        for _ in range(20):  # Newton on the sum of squares
+            E = np.sqrt((s * p1) ** 2 + me ** 2)
+            r = E.sum(1) - mmu
+            dr = (s * p1 ** 2 / E).sum(1)
+            s -= (r * dr).sum() / (dr * dr).sum()
+        return float(s), int(ok.sum()), float(np.sqrt(np.mean(r ** 2)))
+
+    s_fit, n, rms = solve(est)
+    s_truth_align, _, _ = solve(truth)
+    s_nominal, _, _ = solve(np.r_[np.zeros(24), 1.0])
+    return {"signal_decays": n, "injected": float(truth[24]), "recovered": s_fit,
+            "residual": s_fit - float(truth[24]), "recovered_at_true_alignment": s_truth_align,
+            "recovered_at_nominal_alignment": s_nominal, "energy_sum_rms_MeV": rms,
+            "method": "energy sum of the signal decays whose three tracks were kept, curvatures from m3e_fit_kappa "
+                      "at the fitted alignment, least squares in the scale"}
 
 
 MU_RATES = (1e8, 2e8, 5e8, 1e9)
@@ -567,6 +671,8 @@ def main():
             "algorithmic_hbm_bytes": nh * 4 + (nf + 1) * 8 + 2 * nf}
     # the same kernel's use of its issue slots: warp instructions per frame from the ncu
     # capture, over this run's kernel time, against 4 schedulers x SMs x clock
+    roof["ingest"] = ingest_roofline(ctx, hits, dev, stream)
+    roof["compaction"] = compaction_roofline(nf, float(sum(st_ms[i] for i in (0, 1, 2))))
     wi = _recorded("warp_inst_per_frame." + dom["kernel"].split()[0])
     ia = _recorded("issue_active_pct." + dom["kernel"].split()[0])
     if wi is not None and dom["ms"] > 0:

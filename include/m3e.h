@@ -226,15 +226,21 @@ typedef struct {
   int32_t s1_ctas_per_sm;    /* resident CTAs per SM of the stage-1 warp tier */
   int32_t configs_tried;
   float ms_default, ms_best; /* calibration batch time at the defaults and at the choice */
+  int32_t mid_cta_threads;   /* threads of a CTA of the stage-1 middle tier (frames of 161..1024 hits) */
+  int32_t s2_ctas_per_sm;    /* resident CTAs per SM of the track stage */
+  float ms_worst;            /* calibration batch time at the slowest configuration tried */
 } m3e_tuning;
 
 /* Time the staged form on a calibration batch (device buffers as for
- * m3e_select_frames) over a grid of launch parameters and keep the fastest in
- * the context.  Synchronises the context's device; decisions do not depend on
- * the parameters.  Each configuration is timed as the median of five runs
- * after a warm-up; one replaces the current choice only when it is more than
- * 2% faster, so a calibration batch of a few ms keeps the defaults unless a
- * change clearly pays. */
+ * m3e_select_frames) over launch parameters and keep the fastest in the
+ * context: a grid of frames_per_grab (1..16) x defer_hits (96, 128, 160) x
+ * stage-1 CTAs per SM (all, half), then, one axis at a time from that point, the
+ * middle tier's CTA size (128, 256, 512 threads) and the track stage's CTAs per
+ * SM.  Synchronises the context's device; decisions do not depend on the
+ * parameters.  Each configuration is timed as the median of five runs after a
+ * warm-up; one replaces the current choice only when it is more than 2% faster,
+ * so a calibration batch of a few ms keeps the defaults unless a change clearly
+ * pays. */
 int m3e_autotune(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames, uint8_t* d_keep,
                  uint8_t* d_reason, m3e_tuning* out);
 
@@ -330,7 +336,17 @@ int m3e_fit_chi2(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off
                  const int32_t* d_cand, int64_t n_cand, const float* d_params, float* d_chi2_each,
                  cudaStream_t stream);
 
-/* Number of valid candidates of the last m3e_fit_grad / m3e_fit_chi2 call
+/* Weighted mean curvature kappa_bar (1/mm, signed: positive = clockwise turning)
+ * of each frozen candidate's track fit at the given alignment (Sec. "Track
+ * Reconstruction": the inverse-variance mean of the two triplet curvatures), in
+ * d_kappa_each[n_cand] (device float; NaN where the chi2 of m3e_fit_chi2 would be
+ * NaN).  The momentum is p = k B field_scale / |kappa_bar|; a caller fits the field
+ * scale with it (for example from the energy sum of signal decays), since the
+ * chi2 sum cannot (it grows as the square of the scale). */
+int m3e_fit_kappa(m3e_ctx* ctx, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                  const int32_t* d_cand, int64_t n_cand, const float* d_params, float* d_kappa_each,
+                  cudaStream_t stream);
+/* Number of valid candidates of the last m3e_fit_grad / m3e_fit_chi2 / m3e_fit_kappa call
  * (synchronises `stream`). */
 int m3e_fit_valid_count(m3e_ctx* ctx, cudaStream_t stream, int64_t* out);
 

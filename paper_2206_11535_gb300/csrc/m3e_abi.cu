@@ -79,7 +79,7 @@ struct Scratch {
   int64_t hits_cap = 0;
   uint16_t* l3 = nullptr;
   int* fint = nullptr;                      // fstate, ftbase, fntrip, ffound, fncombo
-  long long* fcbase = nullptr;              // fcbase, fhbase
+  long long* fcbase = nullptr;              // per frame: first combination
   int64_t frames_cap = 0;
   int4* trip = nullptr;
   uint8_t* tstatus = nullptr;
@@ -95,6 +95,7 @@ struct m3e_ctx {
   int fused_bpsm = 1, s1_bpsm = 1, s2_bpsm = 1, s3_bpsm = 1, s4_bpsm = 1, s1c_bpsm = 1, s1m_bpsm = 1, ingest_bpsm = 1;
   int grab = 4;
   int defer_hits = W_HITS;
+  int mid_threads = CTA_THREADS;  // threads of a stage-1 middle-tier CTA
   m3e_config cfg{};
   DevCfg dc{};
   float4* col_lut = nullptr;
@@ -185,11 +186,19 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
     d.phs_hi[L] = (float)st;
     d.phs_lo[L] = (float)(st - (double)d.phs_hi[L]);
   }
+  d.pk_nlad = d.pk_ncol = d.pk_nrow = d.pk_coloff = d.pk_rowoff = 0ull;
+  for (int L = 0; L < 4; ++L) {
+    d.pk_nlad |= (unsigned long long)d.nlad[L] << (16 * L);
+    d.pk_ncol |= (unsigned long long)d.ncol[L] << (16 * L);
+    d.pk_nrow |= (unsigned long long)d.nrow[L] << (16 * L);
+    d.pk_coloff |= (unsigned long long)d.col_off[L] << (16 * L);
+    d.pk_rowoff |= (unsigned long long)d.row_off[L] << (16 * L);
+  }
   d.inv_dr01 = (float)(1.0 / (c.r_mm[1] - c.r_mm[0]));
   d.inv_dr12 = (float)(1.0 / (c.r_mm[2] - c.r_mm[1]));
   d.dr12 = (float)(c.r_mm[2] - c.r_mm[1]);
   d.zoff2 = (float)c.half_len_mm[2];
-  d.izw2 = (float)(NB / (2.0 * c.half_len_mm[2]));
+  d.izw2 = (float)(NZB / (2.0 * c.half_len_mm[2]));
   d.c01 = (float)(std::cos(c.phi01_max) * c.r_mm[0] * c.r_mm[1]);
   d.c12 = (float)(std::cos(c.phi12_max) * c.r_mm[1] * c.r_mm[2]);
   d.dl_max = (float)c.dlambda_max;
@@ -261,7 +270,9 @@ int grow(T*& ptr, int64_t& cap, int64_t need, size_t elem, const char* what) {
 constexpr int64_t HITS_PER_FRAME = 128;
 
 int ensure_scratch(Scratch& sc, int64_t nf, bool staged) {
-  const int64_t nh = nf * HITS_PER_FRAME > (1 << 16) ? nf * HITS_PER_FRAME : (1 << 16);
+  // sorted-hit indices travel as int32 in the triplet records: at most 2^31 - 2^16 of them
+  const int64_t nh_want = nf * HITS_PER_FRAME > (1 << 16) ? nf * HITS_PER_FRAME : (1 << 16);
+  const int64_t nh = nh_want < ((int64_t)1 << 31) - (1 << 16) ? nh_want : ((int64_t)1 << 31) - (1 << 16);
   int64_t one = sc.work ? 1 : 0;
   int rc = grow(sc.work, one, 1, 4 * sizeof(int), "work counters");
   if (rc) return rc;
@@ -293,7 +304,7 @@ int ensure_scratch(Scratch& sc, int64_t nf, bool staged) {
     int64_t c0 = sc.frames_cap, c1 = sc.frames_cap, c2 = sc.frames_cap;
     rc = grow(sc.l3, c0, nf, (NB + 1) * sizeof(uint16_t), "layer-3 bins");
     if (!rc) rc = grow(sc.fint, c1, nf, 5 * sizeof(int), "frame state");
-    if (!rc) rc = grow(sc.fcbase, c2, nf, 2 * sizeof(long long), "frame combination and hit bases");
+    if (!rc) rc = grow(sc.fcbase, c2, nf, sizeof(long long), "frame combination bases");
     if (rc) return rc;
     sc.frames_cap = nf;
   }
@@ -345,7 +356,6 @@ SParams staged_params(const Scratch& sc) {
   s.ffound = sc.fint + 3 * F;
   s.fncombo = sc.fint + 4 * F;
   s.fcbase = sc.fcbase;
-  s.fhbase = sc.fcbase + F;
   s.list1 = sc.defer;
   s.list2 = sc.defer2;
   s.list1b = sc.defer1b;
@@ -397,7 +407,7 @@ int enqueue(m3e_ctx* x, Scratch& sc, KParams p, int form, bool debug, cudaStream
                         x->sms * x->s4_bpsm, x->sms * x->s1c_bpsm, x->sms * x->s1m_bpsm};
   const SParams sp = staged_params(sc);
   if (p.gate) CUDA_TRY(cudaMemsetAsync(sp.fstate, 0x7f, sizeof(int) * (size_t)p.n_frames, s));  // no stale states
-  CUDA_TRY(launch_staged(x->dc, p, sp, grids, debug, s, timed ? x->pe : nullptr, after_s1));
+  CUDA_TRY(launch_staged(x->dc, p, sp, grids, debug, s, timed ? x->pe : nullptr, after_s1, x->mid_threads));
   KParams pd = p;  // frames no stage could finish: the CTA-per-frame kernel
   pd.in_list = sp.list2;
   pd.in_count = sp.lcount + 1;
@@ -987,6 +997,45 @@ extern "C" int m3e_autotune(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_
   x->grab = bg;
   x->defer_hits = bd;
   x->s1_bpsm = bb;
+  // then, one axis at a time from that point: the middle tier's CTA size and the
+  // track stage's resident CTAs per SM
+  float worst = best;
+  int bm = x->mid_threads, b2 = x->s2_bpsm;
+  const int s2max = stage_blocks_per_sm(2);
+  const int mids[] = {128, 256, 512};
+  for (int m : mids) {
+    if (rc || m == bm) continue;
+    const int pm = x->mid_threads, pb = x->s1m_bpsm;
+    x->mid_threads = m;
+    x->s1m_bpsm = stage1_mid_blocks_per_sm(m);
+    float ms = 0.f;
+    rc = run(&ms);
+    ++tried;
+    worst = ms > worst ? ms : worst;
+    if (rc == M3E_OK && ms < best * (1.f - AUTOTUNE_MARGIN)) {
+      best = ms;
+      bm = m;
+    } else {
+      x->mid_threads = pm;
+      x->s1m_bpsm = pb;
+    }
+  }
+  const int s2s[] = {s2max, s2max - 1, (s2max + 1) / 2};
+  for (int b : s2s) {
+    if (rc || b < 1 || b == b2) continue;
+    const int pb = x->s2_bpsm;
+    x->s2_bpsm = b;
+    float ms = 0.f;
+    rc = run(&ms);
+    ++tried;
+    worst = ms > worst ? ms : worst;
+    if (rc == M3E_OK && ms < best * (1.f - AUTOTUNE_MARGIN)) {
+      best = ms;
+      b2 = b;
+    } else {
+      x->s2_bpsm = pb;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(st);
@@ -997,6 +1046,9 @@ extern "C" int m3e_autotune(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_
   out->configs_tried = tried;
   out->ms_default = ms_def;
   out->ms_best = best;
+  out->mid_cta_threads = x->mid_threads;
+  out->s2_ctas_per_sm = x->s2_bpsm;
+  out->ms_worst = worst;
   return M3E_OK;
 }
 
@@ -1085,7 +1137,8 @@ int m3e_stream_replay(m3e_ctx* x, const int32_t* h_hits, const int64_t* h_frame_
 namespace {
 
 int fit_call(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n_frames, const int32_t* d_cand,
-             int64_t n_cand, const float* d_params, float* chi2_each, float* chi2_sum, float* grad, cudaStream_t s) {
+             int64_t n_cand, const float* d_params, float* chi2_each, float* chi2_sum, float* grad, cudaStream_t s,
+             float* kappa_each = nullptr) {
   if (!x) return fail(M3E_EINVAL, "ctx is NULL");
   if (n_frames < 0 || n_cand < 0) return fail(M3E_EINVAL, "n_frames and n_cand must be >= 0");
   if (!d_off || !d_params || (n_cand > 0 && (!d_cand || !d_hits)))
@@ -1103,7 +1156,7 @@ int fit_call(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_off, int64_t n_
   if (!x->fit_nvalid) CUDA_TRY(cudaMalloc(&x->fit_nvalid, sizeof(unsigned long long)));
   CUDA_TRY(cudaMemsetAsync(x->fit_nvalid, 0, sizeof(unsigned long long), s));
   CUDA_TRY(launch_fit_grad(x->dc, d_hits, d_off, n_frames, d_cand, n_cand, d_params, x->col_lut, x->row_lut,
-                           x->fit_partial, nb, x->fit_nvalid, chi2_each, chi2_sum, grad, s));
+                           x->fit_partial, nb, x->fit_nvalid, chi2_each, kappa_each, chi2_sum, grad, s));
   return M3E_OK;
 }
 
@@ -1122,6 +1175,14 @@ int m3e_fit_chi2(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_frame_off, 
   if (!d_chi2_each && n_cand > 0) return fail(M3E_EINVAL, "chi2_each must not be NULL");
   return fit_call(x, d_hits, d_frame_off, n_frames, d_cand, n_cand, d_params, d_chi2_each, nullptr, nullptr,
                   stream);
+}
+
+int m3e_fit_kappa(m3e_ctx* x, const int32_t* d_hits, const int64_t* d_frame_off, int64_t n_frames,
+                  const int32_t* d_cand, int64_t n_cand, const float* d_params, float* d_kappa_each,
+                  cudaStream_t stream) {
+  if (!d_kappa_each && n_cand > 0) return fail(M3E_EINVAL, "kappa_each must not be NULL");
+  return fit_call(x, d_hits, d_frame_off, n_frames, d_cand, n_cand, d_params, nullptr, nullptr, nullptr, stream,
+                  d_kappa_each);
 }
 
 int m3e_fit_valid_count(m3e_ctx* x, cudaStream_t stream, int64_t* out) {

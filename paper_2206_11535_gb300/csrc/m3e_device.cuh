@@ -67,12 +67,12 @@ struct FrameSm {
   uint16_t inidx[IDX ? CH : 1];
   uint16_t bstart[NBK + 1];
   uint32_t bcur[kPackB ? NBK / 4 : NBK];  // bucket counts, then cursors
-  // warp stage, selection cuts (warp_cuts): Phi01 partners of a chunk of 32 layer-1
-  // hits, the layer-2 hits in z-bin order (zidx, bin starts zbs) and the candidate
-  // triplets of one round of (layer-1 hit, Phi01 partner) pairs
+  // warp stage, selection cuts (warp_cuts): the layer-2 hits in z-bin order (bin
+  // starts zbs), the (layer-1 hit, Phi01 partner) pairs of a chunk of 32 layer-1 hits
+  // (their layer-0 hits) and the candidate triplets of one round of pairs
+  float4 zq[CH32 == 1 ? 1 : W_L2];  // layer-2 hits in z-bin order: x, y, z, sorted index (as int bits)
   uint8_t p01[CH32 == 1 ? 1 : W_P01];
-  uint8_t zidx[CH32 == 1 ? 1 : W_L2];
-  uint8_t zbs[CH32 == 1 ? 1 : NB + 1];
+  uint8_t zbs[CH32 == 1 ? 1 : NZB + 1];
   alignas(16) uint16_t cand[CH32 == 1 ? 1 : W_CAND];  // also the z-bin counters (32-bit words)
   TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
@@ -95,6 +95,9 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -111,8 +114,19 @@ __device__ __forceinline__ T make_trip(int i0, int i1, int i2) {  // a triplet o
 
 struct Dec {
   int L, g, row, b;
+  int ci, ri;  // indices of the hit's column and row in the look-up tables
   bool ok;
 };
+
+// A per-layer constant selected by the (data-dependent) layer: selects over the
+// four values instead of an indexed load, which the constant cache would serialise
+// over the distinct layers of a warp.
+template <class T>
+__device__ __forceinline__ T by_layer(const T (&v)[4], int L) {
+  return L == 0 ? v[0] : (L == 1 ? v[1] : (L == 2 ? v[2] : v[3]));
+}
+// a 16-bit field of a packed per-layer word
+__device__ __forceinline__ int field16(unsigned long long w, int L) { return (int)((w >> (16 * L)) & 0xffffull); }
 
 __device__ __forceinline__ Dec decode(const DevCfg& C, uint32_t a) {
   Dec d;
@@ -121,11 +135,45 @@ __device__ __forceinline__ Dec decode(const DevCfg& C, uint32_t a) {
   d.row = a & 8191;
   d.ok = (a >> 28) == 0 && lad < C.nlad[d.L] && col < C.ncol[d.L] && d.row < C.nrow[d.L];
   d.g = lad * C.ncol[d.L] + col;
+  d.ci = C.col_off[d.L] + d.g;
+  d.ri = C.row_off[d.L] + d.row;
   // phi bin floor(g NB / ntot) without an integer division: g NB < 2^24 is exact in
   // FP32, and (g NB + 1/2) / ntot lies at least 1/(2 ntot) >= 6e-5 from an integer,
   // far more than the two roundings (< 4e-6 at values below NB)
   d.b = d.ok ? (int)__fmul_rn(__fadd_rn((float)(d.g * NB), 0.5f), C.intot[d.L]) : 0;
   return d;
+}
+
+// decode without the phi bin and without loads indexed by the hit's layer: the
+// per-layer integers come from packed 16-bit fields.  For a kernel that does little
+// else per hit (the ingest), where loads of per-layer constants at the warp's
+// several layers would serialise in the constant cache and bound the kernel.
+__device__ __forceinline__ Dec decode_packed(const DevCfg& C, uint32_t a) {
+  Dec d;
+  d.L = (a >> 26) & 3;
+  const int lad = (a >> 21) & 31, col = (a >> 13) & 255;
+  d.row = a & 8191;
+  const int nlad = field16(C.pk_nlad, d.L), ncol = field16(C.pk_ncol, d.L);
+  d.ok = (a >> 28) == 0 && lad < nlad && col < ncol && d.row < field16(C.pk_nrow, d.L);
+  d.g = lad * ncol + col;
+  d.ci = field16(C.pk_coloff, d.L) + d.g;
+  d.ri = field16(C.pk_rowoff, d.L) + d.row;
+  d.b = 0;
+  return d;
+}
+
+// Azimuth of the centre of global column g of layer L, (g + 1/2) 2 pi / ntot: the
+// step 2 pi / ntot is held as a sum of two floats and the product's rounding error
+// is recovered by a fused multiply-add, which gives the FP64 value rounded once to
+// FP32 for every column of the detector (the look-up table's value, checked
+// exhaustively by the tests).
+template <bool SEL = false>
+__device__ __forceinline__ float column_phi(const DevCfg& C, int L, int g) {
+  const float p = (float)g + 0.5f;  // exact: g < 2^23
+  const float sh = SEL ? by_layer(C.phs_hi, L) : C.phs_hi[L], sl = SEL ? by_layer(C.phs_lo, L) : C.phs_lo[L];
+  const float hi = __fmul_rn(p, sh);
+  const float lo = __fmaf_rn(p, sh, -hi);
+  return __fadd_rn(hi, __fmaf_rn(p, sl, lo));
 }
 
 __device__ __forceinline__ float wrap_2pi(float a) {  // (-2 pi, 2 pi) -> [0, 2 pi)
@@ -752,7 +800,7 @@ __device__ __forceinline__ bool rtc_pass(float x0, float y0, float x1, float y1,
 // [zlo, zhi] lies in bins zbin(zlo) .. zbin(zhi).
 __device__ __forceinline__ int zbin2(float z, const DevCfg& C) {
   const int b = (int)__fmul_rn(__fadd_rn(z, C.zoff2), C.izw2);
-  return b < 0 ? 0 : (b > NB - 1 ? NB - 1 : b);
+  return b < 0 ? 0 : (b > NZB - 1 ? NZB - 1 : b);
 }
 
 // The phi bin of sorted layer-1 hit i: the last bin whose start is at most i (bins
@@ -818,66 +866,74 @@ __device__ __forceinline__ void bucket_scan(const G& g, S& sm) {
 }
 
 // Selection cuts of a warp-stage frame (Algorithm 2), on the hits sorted by (layer,
-// phi bin).  The layer-2 hits are also put in z-bin order (at most W_L2 of them), so
-// that for a (layer-1 hit, Phi01 partner) pair the Delta lambda cut, seen as a z
-// window on the layer-2 hit, becomes a contiguous range of that order.  Per chunk
-// of 32 layer-1 hits (a lane each):
-//   1. the Phi01 partners within the reachable phi bins, stored in a region of p01
-//      reserved by a prefix sum of the window sizes;
-//   2. the Phi12 partners as a bit mask over the z-ordered layer-2 hits, from one
-//      pass over them that all lanes take together;
-//   3. the pairs, numbered by a prefix sum and taken 32 at a time: each lane finds
-//      its pair's layer-1 hit (a search over the lanes' prefix), forms the z window
-//      (widened by 1e-3 mm against rounding) and its bin range, and keeps the Phi12
-//      partners inside it: the candidate triplets, numbered by a prefix sum;
+// phi bin).  The layer-2 hits are also put in z-bin order (x, y, z and index packed
+// in one record), so that for a (layer-1 hit, Phi01 partner) pair the Delta lambda
+// cut, seen as a z window on the layer-2 hit, becomes a contiguous range of that
+// order.  Per chunk of 32 layer-1 hits (a lane each):
+//   1. the Phi01 partners as a bit mask over the layer-0 hits and the Phi12
+//      partners as a bit mask over the z-ordered layer-2 hits, from passes over
+//      those hits that all lanes take together (one broadcast load per hit);
+//   2. the pairs of layer-1 hits that have Phi12 partners, numbered by a prefix sum
+//      and listed with their layer-0 hit;
+//   3. the pairs, 32 at a time: each lane finds its pair's layer-1 hit (a search
+//      over the lanes' prefix), forms the z window (widened by 1e-3 mm against
+//      rounding) and its bin range, and keeps the Phi12 partners inside it: the
+//      candidate triplets, numbered by a prefix sum and listed;
 //   4. the candidates, 32 at a time, through the exact Delta lambda and r_tc tests,
 //      the survivors appended in a fixed order by ballot.
 // The exact tests are the expressions every other stage uses (phi_pass, dl_pass,
 // rtc_pass), and the z window contains every hit that passes Delta lambda, so the
 // selected set equals the brute-force one.  sm.bad = 2 when a capacity is exceeded
 // (the frame goes to a larger stage).  npair / ntt: this lane's share of the pair
-// tests (within the reachable bins) and of the candidate triplets (Phi01 partners
-// times Phi12 partners), the statistics' counts.
+// tests within the reachable phi bins (counted, with stats, as the other stages
+// count them) and of the candidate triplets (Phi01 partners times Phi12 partners).
 template <class S, int CT>
 __device__ __forceinline__ void warp_cuts(S& sm, const DevCfg& C, bool stats, unsigned& npair, unsigned& ntt) {
   const int lane = threadIdx.x & 31;
-  const int l1a = sm.bstart[NB], l1b = sm.bstart[2 * NB], l2b = sm.bstart[3 * NB];
+  const int n0 = sm.bstart[NB], l1a = n0, l1b = sm.bstart[2 * NB], l2b = sm.bstart[3 * NB];
   const int n1 = l1b - l1a, n2 = l2b - l1b;
-  const int nb0 = min(2 * C.k01 + 1, NB), nb2 = min(2 * C.k12 + 1, NB);
-  bool over = n2 > W_L2;
+  bool over = n0 > W_L0 || n2 > W_L2;
   int nt = 0;
   if (!over) {
     // layer-2 hits in z-bin order: counting sort with byte counters packed four to a
-    // word (in the candidate buffer, free until step 3)
+    // word (in the candidate buffer, free until step 3), two hits per lane
     uint32_t* zc = reinterpret_cast<uint32_t*>(sm.cand);
-    if (lane < NB / 4) zc[lane] = 0u;
+    if (lane < NZB / 4) zc[lane] = 0u;
     __syncwarp();
     const int bq0 = lane < n2 ? zbin2(sm.z[l1b + lane], C) : -1;
     const int bq1 = lane + 32 < n2 ? zbin2(sm.z[l1b + lane + 32], C) : -1;
     if (bq0 >= 0) atomicAdd(&zc[bq0 >> 2], 1u << (8 * (bq0 & 3)));
     if (bq1 >= 0) atomicAdd(&zc[bq1 >> 2], 1u << (8 * (bq1 & 3)));
     __syncwarp();
-    const int cb = (int)((zc[lane >> 2] >> (8 * (lane & 3))) & 255u);
-    int inc = cb;
+    const uint32_t w = zc[lane >> 1];  // bins 2 lane, 2 lane + 1
+    const int ca = (int)((w >> (16 * (lane & 1))) & 255u), cb = (int)((w >> (16 * (lane & 1) + 8)) & 255u);
+    int inc = ca + cb;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(FULL, inc, o);
       if (lane >= o) inc += t;
     }
-    sm.zbs[lane] = (uint8_t)(inc - cb);
-    if (lane == 31) sm.zbs[NB] = (uint8_t)inc;
+    const int ex = inc - ca - cb;
+    sm.zbs[2 * lane] = (uint8_t)ex;
+    sm.zbs[2 * lane + 1] = (uint8_t)(ex + ca);
+    if (lane == 31) sm.zbs[NZB] = (uint8_t)inc;
     __syncwarp();
-    if (lane < NB / 4) {
-      uint32_t w = 0;
+    if (lane < NZB / 4) {
+      uint32_t cw = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) w |= (uint32_t)sm.zbs[4 * lane + k] << (8 * k);
-      zc[lane] = w;  // placement cursors
+      for (int k = 0; k < 4; ++k) cw |= (uint32_t)sm.zbs[4 * lane + k] << (8 * k);
+      zc[lane] = cw;  // placement cursors
     }
     __syncwarp();
-    if (bq0 >= 0) sm.zidx[(atomicAdd(&zc[bq0 >> 2], 1u << (8 * (bq0 & 3))) >> (8 * (bq0 & 3))) & 255u] =
-        (uint8_t)(l1b + lane);
-    if (bq1 >= 0) sm.zidx[(atomicAdd(&zc[bq1 >> 2], 1u << (8 * (bq1 & 3))) >> (8 * (bq1 & 3))) & 255u] =
-        (uint8_t)(l1b + lane + 32);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int bq = h ? bq1 : bq0;
+      if (bq >= 0) {
+        const int i2 = l1b + lane + 32 * h;
+        const int pos = (int)((atomicAdd(&zc[bq >> 2], 1u << (8 * (bq & 3))) >> (8 * (bq & 3))) & 255u);
+        sm.zq[pos] = make_float4(sm.x[i2], sm.y[i2], sm.z[i2], __int_as_float(i2));
+      }
+    }
     __syncwarp();
   }
   for (int j0 = 0; j0 < n1 && !over; j0 += 32) {
@@ -885,51 +941,39 @@ __device__ __forceinline__ void warp_cuts(S& sm, const DevCfg& C, bool stats, un
     const bool has = j < n1;
     const int i1 = l1a + j;
     float x1 = 0.f, y1 = 0.f, z1 = 0.f;
-    int n0w = 0, a0 = 0, n0a = 0, n2w = 0;
     if (has) {
       x1 = sm.x[i1];
       y1 = sm.y[i1];
       z1 = sm.z[i1];
-      const int b1 = layer1_bin(sm.bstart, i1);
-      const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
-      a0 = sm.bstart[s0];
-      n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
-      n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
-      if (stats) {
+      if (stats) {  // the pair tests within the reachable phi bins, as the other stages count them
+        const int nb0 = min(2 * C.k01 + 1, NB), nb2 = min(2 * C.k12 + 1, NB);
+        const int b1 = layer1_bin(sm.bstart, i1);
+        const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
         const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
-        n2w = sm.bstart[2 * NB + min(s2 + nb2, NB)] - sm.bstart[2 * NB + s2] +
-              (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - sm.bstart[2 * NB] : 0);
+        npair += sm.bstart[min(s0 + nb0, NB)] - sm.bstart[s0] + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
+        npair += sm.bstart[2 * NB + min(s2 + nb2, NB)] - sm.bstart[2 * NB + s2] +
+                 (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - sm.bstart[2 * NB] : 0);
       }
     }
-    npair += n0w + n2w;
-    // 1. Phi01 partners into regions of p01
-    int e0 = n0w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(FULL, e0, o);
-      if (lane >= o) e0 += t;
+    // 1. Phi01 and Phi12 partners as bit masks (lanes without a layer-1 hit test
+    // (0, 0), which passes neither cut)
+    uint32_t a0 = 0u, a1 = 0u, b0 = 0u, b1 = 0u;
+    const int n0a = min(n0, 32), n2a = min(n2, 32);
+    for (int q = 0; q < n0a; ++q)
+      if (phi_pass(sm.x[q], sm.y[q], x1, y1, C.c01)) a0 |= 1u << q;
+    for (int q = 32; q < n0; ++q)
+      if (phi_pass(sm.x[q], sm.y[q], x1, y1, C.c01)) a1 |= 1u << (q - 32);
+    for (int q = 0; q < n2a; ++q) {
+      const float4 h = sm.zq[q];
+      if (phi_pass(x1, y1, h.x, h.y, C.c12)) b0 |= 1u << q;
     }
-    const int r0 = e0 - n0w;
-    if (__shfl_sync(FULL, e0, 31) > W_P01) {
-      over = true;
-      break;
+    for (int q = 32; q < n2; ++q) {
+      const float4 h = sm.zq[q];
+      if (phi_pass(x1, y1, h.x, h.y, C.c12)) b1 |= 1u << (q - 32);
     }
-    int c01 = 0;
-    for (int k = 0; k < n0w; ++k) {
-      const int i0 = k < n0a ? a0 + k : k - n0a;
-      if (phi_pass(sm.x[i0], sm.y[i0], x1, y1, C.c01)) sm.p01[r0 + c01++] = (uint8_t)i0;
-    }
-    // 2. Phi12 partners: bit q of (mlo, mhi) for z-ordered layer-2 hit q
-    uint32_t mlo = 0u, mhi = 0u;
-    for (int q = 0; q < n2; ++q) {
-      const int i2 = sm.zidx[q];
-      const uint32_t pp = phi_pass(x1, y1, sm.x[i2], sm.y[i2], C.c12) ? 1u : 0u;
-      if (q < 32) mlo |= pp << q;
-      else mhi |= pp << (q - 32);
-    }
-    const int c12all = __popc(mlo) + __popc(mhi);
+    const int c01 = __popc(a0) + __popc(a1), c12all = __popc(b0) + __popc(b1);
     ntt += (unsigned)(c01 * c12all);
-    // 3. pairs whose layer-1 hit has Phi12 partners
+    // 2. the pairs whose layer-1 hit has Phi12 partners, listed by their layer-0 hit
     const int pc = c12all ? c01 : 0;
     int pe = pc;
 #pragma unroll
@@ -939,6 +983,17 @@ __device__ __forceinline__ void warp_cuts(S& sm, const DevCfg& C, bool stats, un
     }
     const int pre = pe - pc;
     const int T = __shfl_sync(FULL, pe, 31);
+    if (T > W_P01) {
+      over = true;
+      break;
+    }
+    if (pc) {
+      int wpos = pre;
+      for (uint32_t m = a0; m; m &= m - 1u) sm.p01[wpos++] = (uint8_t)(__ffs(m) - 1);
+      for (uint32_t m = a1; m; m &= m - 1u) sm.p01[wpos++] = (uint8_t)(__ffs(m) + 31);
+    }
+    __syncwarp();
+    // 3. the pairs, 32 at a time
     for (int k0 = 0; k0 < T; k0 += 32) {
       const int k = k0 + lane;
       int ow = 0;  // the last lane whose pairs start at or before k
@@ -947,14 +1002,15 @@ __device__ __forceinline__ void warp_cuts(S& sm, const DevCfg& C, bool stats, un
         const int pv = __shfl_sync(FULL, pre, ow + st);
         if (pv <= k) ow += st;
       }
-      const int pre_o = __shfl_sync(FULL, pre, ow), r0_o = __shfl_sync(FULL, r0, ow);
       const float px1 = __shfl_sync(FULL, x1, ow), py1 = __shfl_sync(FULL, y1, ow), pz1 = __shfl_sync(FULL, z1, ow);
-      const uint32_t pml = __shfl_sync(FULL, mlo, ow), pmh = __shfl_sync(FULL, mhi, ow);
+      const uint32_t pml = __shfl_sync(FULL, b0, ow), pmh = __shfl_sync(FULL, b1, ow);
       int i0 = 0;
-      float tl01 = 0.f;
+      float x0 = 0.f, y0 = 0.f, tl01 = 0.f;
       unsigned long long cm = 0ull;
       if (k < T) {
-        i0 = sm.p01[r0_o + (k - pre_o)];
+        i0 = sm.p01[k];
+        x0 = sm.x[i0];
+        y0 = sm.y[i0];
         tl01 = tan_l01(sm.z[i0], pz1, C);
         const float zlo = pz1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
         const float zhi = pz1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
@@ -963,6 +1019,7 @@ __device__ __forceinline__ void warp_cuts(S& sm, const DevCfg& C, bool stats, un
         const unsigned long long below_lo = lo >= 64 ? ~0ull : (1ull << lo) - 1ull;
         cm = (below_hi & ~below_lo) & (((unsigned long long)pmh << 32) | pml);
       }
+      const int tri01 = i0 | ((l1a + j0 + ow) << 8);  // the pair's layer-0 and layer-1 sorted indices
       const int cnt = __popcll(cm);
       int ce = cnt;
 #pragma unroll
@@ -980,25 +1037,21 @@ __device__ __forceinline__ void warp_cuts(S& sm, const DevCfg& C, bool stats, un
           if (idx >= c0 && idx < c0 + W_CAND) sm.cand[idx - c0] = (uint16_t)((lane << 6) | q);
         }
         __syncwarp();
+        // 4. the exact tests, 32 candidates at a time
         const int ne = min(ctot - c0, W_CAND);
         for (int e0 = 0; e0 < ne; e0 += 32) {
           const int e = e0 + lane;
           const int ent = e < ne ? sm.cand[e] : 0;
           const int pl = ent >> 6;
-          const int ci0 = __shfl_sync(FULL, i0, pl), cow = __shfl_sync(FULL, ow, pl);
-          const float ctl = __shfl_sync(FULL, tl01, pl);
-          const float cx1 = __shfl_sync(FULL, px1, pl), cy1 = __shfl_sync(FULL, py1, pl),
-                      cz1 = __shfl_sync(FULL, pz1, pl);
-          bool pass = false;
-          int ci2 = 0;
-          if (e < ne) {
-            ci2 = sm.zidx[ent & 63];
-            const float x2 = sm.x[ci2], y2 = sm.y[ci2];
-            pass = dl_pass(cz1, sm.z[ci2], ctl, C) && rtc_pass(sm.x[ci0], sm.y[ci0], cx1, cy1, x2, y2, C);
-          }
+          const float cx0 = __shfl_sync(FULL, x0, pl), cy0 = __shfl_sync(FULL, y0, pl);
+          const float cx1 = __shfl_sync(FULL, px1, pl), cy1 = __shfl_sync(FULL, py1, pl);
+          const float cz1 = __shfl_sync(FULL, pz1, pl), ctl = __shfl_sync(FULL, tl01, pl);
+          const int ct = __shfl_sync(FULL, tri01, pl);
+          const float4 h = sm.zq[ent & 63];
+          const bool pass = e < ne && dl_pass(cz1, h.z, ctl, C) && rtc_pass(cx0, cy0, cx1, cy1, h.x, h.y, C);
           const unsigned bm = __ballot_sync(FULL, pass);
           const int kk = nt + __popc(bm & ((1u << lane) - 1u));
-          if (pass && kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(ci0, l1a + j0 + cow, ci2);
+          if (pass && kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(ct & 255, ct >> 8, __float_as_int(h.w));
           nt += __popc(bm);
         }
         __syncwarp();
@@ -1024,11 +1077,20 @@ constexpr int PENDING = -2;  // frame_front result: triplets selected, later sta
 // LIVE: the hits sit in a ring that the host rewrites while the kernel runs
 // (streaming), so they are read with loads that bypass the caches instead of
 // the read-only path.
+// prefetch_next: the group takes frame f + 1 next; its addresses are fetched into
+// L1 while this frame is processed.
 template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG, bool LIVE = false>
-__device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P, int f) {
+__device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P, int f, bool prefetch_next = false) {
   const bool stats = P.stats != nullptr;
   const int64_t base = P.off[f] - P.off_base;
   const int64_t n64 = P.off[f + 1] - P.off[f];
+  if constexpr (G::N == 32 && !LIVE) {
+    if (prefetch_next) {
+      const int64_t nb = P.off[f + 1] - P.off_base, ne = P.off[f + 2] - P.off_base;
+      const int64_t a = nb + 32 * g.rank();
+      if (g.rank() < 8 && a < ne) prefetch_l1(P.hits + a);
+    }
+  }
   if (DEBUG && g.leader()) {
     P.dump.n_trip[f] = 0;
     P.dump.n_combo[f] = 0;
@@ -1093,11 +1155,11 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
       if (i < n) {
         const Dec d = decode(C, av[k]);
         const int pos = bucket_add(sm, d.L * NB + d.b);
-        const float* cl = reinterpret_cast<const float*>(P.col_lut + C.col_off[d.L] + d.g);
+        const float* cl = reinterpret_cast<const float*>(P.col_lut + d.ci);
         cp_async4(&sm.x[pos], cl);
         cp_async4(&sm.y[pos], cl + 1);
         if constexpr (S::kPhi) cp_async4(&sm.phi[pos], cl + 2);
-        cp_async4(&sm.z[pos], P.row_lut + C.row_off[d.L] + d.row);
+        cp_async4(&sm.z[pos], P.row_lut + d.ri);
         if constexpr (S::kAddr) sm.addr[pos] = av[k];
         if constexpr (S::kIdx) sm.inidx[pos] = (uint16_t)i;
       }
@@ -1127,11 +1189,11 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
       const Dec d = decode(C, a);
       const int key = d.L * NB + d.b;
       const int pos = bucket_add(sm, key);
-      const float4 c4 = __ldg(P.col_lut + C.col_off[d.L] + d.g);
+      const float4 c4 = __ldg(P.col_lut + d.ci);
       sm.x[pos] = c4.x;
       sm.y[pos] = c4.y;
       if constexpr (S::kPhi) sm.phi[pos] = c4.z;
-      sm.z[pos] = __ldg(P.row_lut + C.row_off[d.L] + d.row);
+      sm.z[pos] = __ldg(P.row_lut + d.ri);
       if constexpr (S::kAddr) sm.addr[pos] = a;
       if constexpr (S::kIdx) sm.inidx[pos] = (uint16_t)i;
     }

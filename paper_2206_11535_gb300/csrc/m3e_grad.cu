@@ -238,6 +238,7 @@ struct GradParams {
   const float* row_lut;
   double* partial;                 // [gridDim.x][NG]
   float* chi2_each;                // or nullptr
+  float* kappa_each;               // or nullptr: the weighted mean curvature of each fit
   unsigned long long* n_valid;     // candidates with a finite chi2 and gradient
   int grad;
 };
@@ -284,6 +285,7 @@ __global__ void __launch_bounds__(GT) k_fit_grad(const __grid_constant__ DevCfg 
       for (int r = 0; r < 3; ++r) P[L][r] = R[3 * r] * X[L][0] + R[3 * r + 1] * X[L][1] + R[3 * r + 2] * X[L][2] + A.d[L][r];
     }
     float chi2 = __int_as_float(0x7fc00000);  // NaN unless the fit succeeds
+    float kb_out = __int_as_float(0x7fc00000);
     if (ok) {
       const TFitF f1 = fit_triplet(P[0][0], P[0][1], P[0][2], P[1][0], P[1][1], P[1][2], P[2][0], P[2][1], P[2][2],
                                    C.hl[1], kB);
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(GT) k_fit_grad(const __grid_constant__ DevCfg 
         ok = kb != 0.f && isfinite(kb);
       }
       if (ok) {
+        kb_out = kb;
         const float Rb = 1.f / fabsf(kb);
         const float pb = kB * Rb;
         chi2 = kink_chi2(f1, Rb, pb * C.ihl[1]) + kink_chi2(f2, Rb, pb * C.ihl[2]);
@@ -378,6 +381,7 @@ __global__ void __launch_bounds__(GT) k_fit_grad(const __grid_constant__ DevCfg 
       ++nvalid;
     }
     if (G.chi2_each) G.chi2_each[i] = ok ? chi2 : __int_as_float(0x7fc00000);
+    if (G.kappa_each) G.kappa_each[i] = ok ? kb_out : __int_as_float(0x7fc00000);
   }
   // block sums in FP64, fixed order
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -425,7 +429,7 @@ int fit_grad_partial_size() { return NG; }
 cudaError_t launch_fit_grad(const DevCfg& c, const int32_t* hits, const int64_t* off, int64_t n_frames,
                             const int32_t* cand, int64_t n_cand, const float* params, const float4* col_lut,
                             const float* row_lut, double* partial, int nblocks, unsigned long long* n_valid,
-                            float* chi2_each, float* chi2_sum, float* grad, cudaStream_t s) {
+                            float* chi2_each, float* kappa_each, float* chi2_sum, float* grad, cudaStream_t s) {
   GradParams g{};
   g.hits = hits;
   g.off = off;
@@ -437,6 +441,7 @@ cudaError_t launch_fit_grad(const DevCfg& c, const int32_t* hits, const int64_t*
   g.row_lut = row_lut;
   g.partial = partial;
   g.chi2_each = chi2_each;
+  g.kappa_each = kappa_each;
   g.n_valid = n_valid;
   if (grad) k_fit_grad<true><<<nblocks, GT, 0, s>>>(c, g);
   else k_fit_grad<false><<<nblocks, GT, 0, s>>>(c, g);

@@ -25,24 +25,17 @@ struct Coord {
   float x, y, z, phi;
 };
 
-__device__ __forceinline__ float column_phi(const DevCfg& C, int L, int g) {
-  const float p = (float)g + 0.5f;  // exact: g < 2^23
-  const float hi = __fmul_rn(p, C.phs_hi[L]);
-  const float lo = __fmaf_rn(p, C.phs_hi[L], -hi);  // the product's rounding error, exactly
-  return __fadd_rn(hi, __fmaf_rn(p, C.phs_lo[L], lo));
-}
-
 template <bool PHI>
 __device__ __forceinline__ Coord ingest_one(const DevCfg& C, const float2* __restrict__ xy, const float* __restrict__ zr,
                                             uint32_t a, bool& bad) {
-  const Dec d = decode(C, a);
+  const Dec d = decode_packed(C, a);
   Coord c;
   if (d.ok) {
-    const float2 q = xy[C.col_off[d.L] + d.g];
+    const float2 q = xy[d.ci];
     c.x = q.x;
     c.y = q.y;
-    c.z = zr[C.row_off[d.L] + d.row];
-    c.phi = PHI ? column_phi(C, d.L, d.g) : 0.f;
+    c.z = zr[d.ri];
+    c.phi = PHI ? column_phi<true>(C, d.L, d.g) : 0.f;
   } else {
     bad = true;
     c.x = c.y = c.z = c.phi = __int_as_float(0x7fc00000);  // quiet NaN

@@ -17,7 +17,8 @@ constexpr int DEFERRED = -1;      // process_frame result: frame too large for t
 // whose capacities are the configuration limits.
 constexpr int W_HITS = 160, W_TRIP = 160, W_TRK = 48, W_COMBO = 512;
 constexpr int W_P01 = 384;        // warp stage: Phi01 partners of 32 layer-1 hits
-constexpr int W_L2 = 64;          // warp stage: layer-2 hits (bit masks of two words)
+constexpr int W_L0 = 64, W_L2 = 64;  // warp stage: layer-0 / layer-2 hits (bit masks of two words)
+constexpr int NZB = 64;           // warp stage: z bins of the layer-2 order
 constexpr int W_CAND = 256;       // warp stage: candidate triplets written per step
 constexpr int C_HITS = 4096, C_TRIP = 1024, C_TRK = 128, C_COMBO = 1024;
 constexpr int WARPS_PER_CTA = 4;  // persistent warp kernel: warps (frames in flight) per CTA
@@ -29,7 +30,7 @@ struct DevCfg {
   float r[4];
   float inv_dr01, inv_dr12;   // 1/(r1 - r0), 1/(r2 - r1), nominal radii
   float dr12;                 // r2 - r1
-  float zoff2, izw2;          // layer-2 z bin of the warp stage: (z + zoff2) * izw2, NB bins over the length
+  float zoff2, izw2;          // layer-2 z bin of the warp stage: (z + zoff2) * izw2, NZB bins over the length
   float c01, c12;             // cos(phi_max) * r_i * r_j: a pair passes when h_i . h_j >= c
   float dl_max;               // |Delta lambda| <= dl_max
   float rtc_lo2, rtc_hi2;     // (2 rtc_min)^2, (2 rtc_max)^2 against (d01 d12 d20)^2 / cross^2
@@ -38,6 +39,9 @@ struct DevCfg {
   float intot[4];             // 1 / ntot, rounded once (phi bin of a column, decode)
   float phs_hi[4], phs_lo[4]; // 2 pi / ntot as a sum of two floats (phi of a column by exact FP32 steps)
   int col_off[4], row_off[4]; // offsets of each layer in the look-up tables
+  // the same per-layer integers packed as 16-bit fields (layer L in bits 16 L ..), read
+  // by decode with shifts instead of loads indexed by the hit's layer
+  unsigned long long pk_nlad, pk_ncol, pk_nrow, pk_coloff, pk_rowoff;
   float kB;                   // p [MeV] = kB * R [mm]
   float hl[4];                // Highland width numerator: sigma_MS(p) = hl[layer] / p
   float ihl[4];               // 1 / hl
@@ -80,7 +84,6 @@ struct SParams {
   float4* hp;                  // sorted hits of the pending frames (from the hit allocator): x, y, z, phi
   uint32_t* haddr;
   uint16_t* hidx;              // input index of each sorted hit (candidate record only)
-  long long* fhbase;           // per frame: first sorted hit
   int* list1;                  // frames deferred by the warp tier of stage 1
   int* list1b;                 // frames deferred by the middle tier of stage 1
   int* list2;                  // frames deferred by the top tier of stage 1 and by stage 3
@@ -89,7 +92,7 @@ struct SParams {
   int *fstate, *ftbase, *fntrip, *ffound;  // per frame: state, triplet range, vertex found
   long long* fcbase;           // per frame: first combination
   int* fncombo;
-  int4* trip;                  // {frame, i0, i1, i2} (frame-relative sorted indices), frame -1 = unused
+  int4* trip;                  // {frame, first sorted hit, i0 | i1 << 16, i2} (frame-relative indices), frame -1 = unused
   uint8_t* tstatus;            // per triplet: track status
   float4* trec;                // per triplet: 16-float track record when kept
   int4* combo;                 // {frame, triplet a, triplet b, triplet e-}, frame -1 = unused
@@ -107,7 +110,8 @@ cudaError_t launch_fused(const DevCfg& c, const KParams& p, int grid, bool debug
 cudaError_t launch_deferred(const DevCfg& c, const KParams& p, int grid, bool debug, cudaStream_t s);
 cudaError_t launch_plain(const DevCfg& c, const KParams& p, bool debug, cudaStream_t s);
 cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
-                          cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1 = nullptr);
+                          cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1 = nullptr, int mid_threads = 256);
+int stage1_mid_blocks_per_sm(int threads);  // resident CTAs per SM of the stage-1 middle tier
 size_t stage1c_smem_bytes();
 int fused_blocks_per_sm();
 int stage_blocks_per_sm(int stage);
@@ -125,7 +129,7 @@ int fit_grad_partial_size();
 cudaError_t launch_fit_grad(const DevCfg& c, const int32_t* hits, const int64_t* off, int64_t n_frames,
                             const int32_t* cand, int64_t n_cand, const float* params, const float4* col_lut,
                             const float* row_lut, double* partial, int nblocks, unsigned long long* n_valid,
-                            float* chi2_each, float* chi2_sum, float* grad, cudaStream_t s);
+                            float* chi2_each, float* kappa_each, float* chi2_sum, float* grad, cudaStream_t s);
 
 // Records the calling thread's error message (m3e_last_error_string) and returns code.
 int m3e_set_error(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));

@@ -18,9 +18,10 @@ namespace {
 
 constexpr int NL3 = NB + 1;                        // layer-3 bin starts per frame
 constexpr int S1_TRIP = 160;                       // stage-1 warp-tier triplet capacity
-// phi and the address of each hit at hand for the emit (no global re-reads)
-using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1>;
-using SmFrontD = FrameSm<W_HITS, S1_TRIP, 1, 1>;                // candidate record: with input indices
+// the address of each hit at hand for the emit (its phi is computed there); input
+// indices only for the candidate record
+using SmFront = FrameSm<W_HITS, S1_TRIP, 1, 1, false, false, true>;
+using SmFrontD = FrameSm<W_HITS, S1_TRIP, 1, 1, false, true, true>;
 constexpr int M_HITS = 1024;                       // stage-1 middle tier (CTA per frame)
 using SmFrontMid = FrameSm<M_HITS, C_TRIP, 1, 1>;
 using SmFrontCta = FrameSm<C_HITS, C_TRIP, 1, 1>;
@@ -45,27 +46,21 @@ __device__ __forceinline__ int warp_count_add(int* ctr, bool pred) {  // ordered
 }
 
 // ---- stage 1: write-out of a frame whose cuts selected triplets
-// Sorted hits and triplets go to global memory at places taken from the hit and
-// triplet allocators; a frame that does not fit is deferred (returns false).
+// The sorted hits of frame f take the places of its input hits (off[f] - off_base
+// onwards, so no allocator is needed); its triplets go to a range taken from the
+// triplet allocator, whose atomic is issued first and waited for only after the
+// hits are written.  A frame that does not fit is deferred (returns false).
 template <class G, class Sm, bool DEBUG, bool LIVE = false>
 __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, const KParams& P, const SParams& S,
                                            int f, int n, int ntrip, long long* bcast) {
-  if (g.leader()) {
-    bcast[0] = (long long)atomicAdd(&S.counters[3], (unsigned long long)n);
-    bcast[1] = (long long)atomicAdd(&S.counters[0], (unsigned long long)ntrip);
-  }
-  g.sync();
-  const long long hb = bcast[0], tb = bcast[1];
-  g.sync();
-  if (hb + n > S.hits_cap || tb + ntrip > S.trip_cap) {
-    // out of space: mark the triplet slots this frame owns below the cap as unused
-    for (int64_t t = tb + g.rank(); t < S.trip_cap && t < tb + ntrip; t += G::N) S.trip[t] = make_int4(-1, 0, 0, 0);
-    return false;
-  }
+  long long tb = 0;
+  if (g.leader()) tb = (long long)atomicAdd(&S.counters[0], (unsigned long long)ntrip);
+  const long long hb = P.off[f] - P.off_base;
+  const bool hits_fit = hb + n <= S.hits_cap;
   // phi and the address of a sorted hit serve only the layer-3 search of stage 2
   const int l3s = sm.bstart[3 * NB];
-  const int32_t* hin = P.hits + (P.off[f] - P.off_base);
-  for (int i = g.rank(); i < n; i += G::N) {
+  const int32_t* hin = P.hits + hb;
+  for (int i = g.rank(); hits_fit && i < n; i += G::N) {
     float phi = 0.f;
     if (i >= l3s) {
       uint32_t a;
@@ -75,7 +70,7 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, 
         phi = sm.phi[i];
       } else {
         const Dec d = decode(C, a);
-        phi = __ldg(P.col_lut + C.col_off[d.L] + d.g).z;
+        phi = column_phi(C, d.L, d.g);
       }
       S.haddr[hb + i] = a;
     }
@@ -85,14 +80,26 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, 
       S.hidx[hb + i] = sm.inidx[i];
     }
   }
+  if constexpr (G::N == 32) {
+    tb = __shfl_sync(FULL, tb, 0);
+  } else {
+    if (g.leader()) bcast[1] = tb;
+    g.sync();
+    tb = bcast[1];
+    g.sync();
+  }
+  if (!hits_fit || tb + ntrip > S.trip_cap) {
+    // out of space: mark the triplet slots this frame owns below the cap as unused
+    for (int64_t t = tb + g.rank(); t < S.trip_cap && t < tb + ntrip; t += G::N) S.trip[t] = make_int4(-1, 0, 0, 0);
+    return false;
+  }
   for (int b = g.rank(); b < NL3; b += G::N) S.l3[(int64_t)f * NL3 + b] = sm.bstart[3 * NB + b];
   for (int t = g.rank(); t < ntrip; t += G::N) {
     const auto q = sm.u.trip[t];
-    S.trip[tb + t] = make_int4(f, q.x, q.y, q.z);
+    S.trip[tb + t] = make_int4(f, (int)hb, (int)q.x | ((int)q.y << 16), (int)q.z);
   }
   if (g.leader()) {
     S.fstate[f] = PENDING;
-    S.fhbase[f] = hb;
     S.ftbase[f] = (int)tb;
     S.fntrip[f] = ntrip;
     S.ffound[f] = 0;
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
           arrived = k;
         }
       }
-      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED>(g, sm, C, P, f);
+      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED>(g, sm, C, P, f, f + 1 < f1);
       stage1_finish<WarpGroup, Sm, DEBUG, GATED>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
     }
   }
@@ -204,21 +211,22 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
 
 // ---- stage 1, CTA tiers: one CTA per frame deferred by the tier below (large
 // frames); the middle tier stages up to M_HITS hits, the top tier C_HITS.
-template <class Sm, int CH, bool DEBUG>
-__global__ void __launch_bounds__(CTA_THREADS)
+// NT: threads of a CTA (the middle tier's is a tuning parameter).
+template <class Sm, int CH, bool DEBUG, int NT = CTA_THREADS>
+__global__ void __launch_bounds__(NT)
     k_stage1c(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sm& sm = *reinterpret_cast<Sm*>(smem_raw);
   __shared__ long long bcast[2];
-  const CtaGroup<CTA_THREADS> g;
+  const CtaGroup<NT> g;
   clear_stats(g, sm);
   const int count = *P.in_count;
   for (int i = blockIdx.x; i < count; i += gridDim.x) {
     const int f = P.in_list[i];
     int r;
     if (CH < C_HITS && P.off[f + 1] - P.off[f] > CH) r = DEFERRED;  // for the next tier
-    else r = frame_front<CtaGroup<CTA_THREADS>, Sm, CH, C_TRIP, false, DEBUG>(g, sm, C, P, f);
-    stage1_finish<CtaGroup<CTA_THREADS>, Sm, DEBUG>(g, sm, C, P, S, f, r, bcast);
+    else r = frame_front<CtaGroup<NT>, Sm, CH, C_TRIP, false, DEBUG>(g, sm, C, P, f);
+    stage1_finish<CtaGroup<NT>, Sm, DEBUG>(g, sm, C, P, S, f, r, bcast);
   }
   flush_stats(g, sm, P.stats);
 }
@@ -228,14 +236,21 @@ template <bool DEBUG>
 __global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM: latency hiding over a few spilled registers
     k_stage2(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   const int64_t n = min((int64_t)S.counters[0], S.trip_cap);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int4 r = S.trip[i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int4 rn = i < n ? S.trip[i] : make_int4(-1, 0, 0, 0);
+  for (; i < n; i += stride) {
+    // the record carries the frame, its first sorted hit and the three frame-relative
+    // indices; the next record is loaded while this triplet is fitted
+    const int4 r = rn;
+    if (i + stride < n) rn = S.trip[i + stride];
     const int f = r.x;
     if (f < 0) continue;
-    const int64_t base = S.fhbase[f];
+    const int64_t base = (int64_t)(unsigned)r.y;
+    const int i0 = r.z & 0xffff, i1 = (int)((unsigned)r.z >> 16), i2 = r.w;
     const GHits v{S.hp + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
     float tk[14];
-    const TrackOut o = build_track(v, C, r.y, r.z, r.w, tk);
+    const TrackOut o = build_track(v, C, i0, i1, i2, tk);
     S.tstatus[i] = (uint8_t)o.status;
     if (o.status == 5) {
       float4* q = S.trec + 4 * i;
@@ -248,9 +263,9 @@ __global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM: latency hiding over
       const int t = (int)(i - S.ftbase[f]);
       if (t < P.dump.cap_trip) {
         const int64_t d = (int64_t)f * P.dump.cap_trip + t;
-        P.dump.trip[4 * d + 0] = S.hidx[base + r.y];
-        P.dump.trip[4 * d + 1] = S.hidx[base + r.z];
-        P.dump.trip[4 * d + 2] = S.hidx[base + r.w];
+        P.dump.trip[4 * d + 0] = S.hidx[base + i0];
+        P.dump.trip[4 * d + 1] = S.hidx[base + i1];
+        P.dump.trip[4 * d + 2] = S.hidx[base + i2];
         P.dump.trip[4 * d + 3] = o.i3 >= 0 ? (int)S.hidx[base + o.i3] : -1;
         P.dump.trk_status[d] = o.status;
         P.dump.trk_val[4 * d + 0] = o.kbar;
@@ -594,13 +609,26 @@ int stage_blocks_per_sm(int stage) {
   return e == cudaSuccess && nb > 0 ? nb : 1;
 }
 
+template <int NT>
+int mid_blocks_per_sm_t() {
+  int nb = 0;
+  set_smem(k_stage1c<SmFrontMid, M_HITS, false, NT>, stage1m_smem_bytes());
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, k_stage1c<SmFrontMid, M_HITS, false, NT>, NT, stage1m_smem_bytes());
+  return e == cudaSuccess && nb > 0 ? nb : 1;
+}
+
+int stage1_mid_blocks_per_sm(int threads) {
+  return threads == 128 ? mid_blocks_per_sm_t<128>() : (threads == 512 ? mid_blocks_per_sm_t<512>() : mid_blocks_per_sm_t<256>());
+}
+
 // Stage 1 (warp tier; middle CTA tier over the warp tier's deferred frames; top
 // CTA tier over the middle tier's), stages 2-5.  grids: stage 1 warp tier, 2, 3,
 // 4, stage 1 top tier, stage 1 middle tier.  Frames deferred by the top tier or by
 // stage 3 end up in S.list2 for the caller's CTA-per-frame kernel.  ev (9 events or
 // null): before stage 1 and after each kernel.
 cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
-                          cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1) {
+                          cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1, int mid_threads) {
   const size_t sm1 = stage1_smem_bytes(debug), smc = stage1c_smem_bytes(), smm = stage1m_smem_bytes();
   const bool gated = p.gate != nullptr && !debug;
   cudaError_t e = debug ? set_smem(k_stage1<true>, sm1)
@@ -630,8 +658,19 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   // the later kernels read the hits too: order them after every copy of the host entry
   if (after_s1) cudaStreamWaitEvent(st, after_s1, 0);
   if (ev) cudaEventRecord(ev[1], st);
-  if (debug) k_stage1c<SmFrontMid, M_HITS, true><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
-  else k_stage1c<SmFrontMid, M_HITS, false><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
+  if (debug) {
+    k_stage1c<SmFrontMid, M_HITS, true><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
+  } else if (mid_threads == 128) {
+    e = set_smem(k_stage1c<SmFrontMid, M_HITS, false, 128>, smm);
+    if (e != cudaSuccess) return e;
+    k_stage1c<SmFrontMid, M_HITS, false, 128><<<grids[5], 128, smm, st>>>(c, pm, s);
+  } else if (mid_threads == 512) {
+    e = set_smem(k_stage1c<SmFrontMid, M_HITS, false, 512>, smm);
+    if (e != cudaSuccess) return e;
+    k_stage1c<SmFrontMid, M_HITS, false, 512><<<grids[5], 512, smm, st>>>(c, pm, s);
+  } else {
+    k_stage1c<SmFrontMid, M_HITS, false><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
+  }
   if (ev) cudaEventRecord(ev[2], st);
   if (debug) k_stage1c<SmFrontCta, C_HITS, true><<<grids[4], CTA_THREADS, smc, st>>>(c, pc, s);
   else k_stage1c<SmFrontCta, C_HITS, false><<<grids[4], CTA_THREADS, smc, st>>>(c, pc, s);

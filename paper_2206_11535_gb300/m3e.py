@@ -58,7 +58,8 @@ class Dump(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("frames_per_grab", C.c_int32), ("defer_hits", C.c_int32), ("s1_ctas_per_sm", C.c_int32),
-                ("configs_tried", C.c_int32), ("ms_default", C.c_float), ("ms_best", C.c_float)]
+                ("configs_tried", C.c_int32), ("ms_default", C.c_float), ("ms_best", C.c_float),
+                ("mid_cta_threads", C.c_int32), ("s2_ctas_per_sm", C.c_int32), ("ms_worst", C.c_float)]
 
 
 class Result(C.Structure):
@@ -113,6 +114,7 @@ def _load(path: str = LIB_PATH):
     lib.m3e_set_profiling.argtypes = [vp, C.c_int]
     lib.m3e_fit_grad.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
     lib.m3e_fit_chi2.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp]
+    lib.m3e_fit_kappa.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp]
     lib.m3e_fit_valid_count.argtypes = [vp, vp, C.POINTER(C.c_int64)]
     lib.m3e_stream_open.argtypes = [vp, C.POINTER(StreamParams)]
     lib.m3e_stream_submit.argtypes = [vp, vp, C.c_int32, C.c_uint64, vp]
@@ -365,6 +367,15 @@ class Context:
         out = torch.empty(c.shape[0], dtype=torch.float32, device=hits.device)
         _check(lib.m3e_fit_chi2(self._h, _ptr(hits), _ptr(off), off.numel() - 1, _ptr(c), c.shape[0],
                                 _ptr(params.contiguous()), _ptr(out), _stream(stream)))
+        return out
+
+    def fit_kappa(self, hits, off, cand, params, stream=None):
+        """``m3e_fit_kappa``: the weighted mean curvature of each candidate's fit (NaN where left out)."""
+        import torch
+        c = cand.contiguous()
+        out = torch.empty(c.shape[0], dtype=torch.float32, device=hits.device)
+        _check(lib.m3e_fit_kappa(self._h, _ptr(hits), _ptr(off), off.numel() - 1, _ptr(c), c.shape[0],
+                                 _ptr(params.contiguous()), _ptr(out), _stream(stream)))
         return out
 
     def fit_valid_count(self, stream=None) -> int:

@@ -11,11 +11,15 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-# Tolerances.  chi2 of one candidate: FP32 fit vs FP64 (as for the selection's
-# derived quantities).  Gradient: relative to the largest component, as the sum
-# over candidates of terms of both signs can cancel in a single component.
-CHI2_REL, CHI2_ABS = 2e-3, 2e-3
+# Tolerances.  chi2 of one candidate: FP32 fit vs FP64, relative to the value plus
+# the track-chi2 band of the selection's parity check (2e-4 of the cut, 32), which
+# also covers the displaced geometries.  Gradient: every component within 1e-3 of
+# itself, plus a noise floor GRAD_FLOOR times the largest component: a component
+# is a sum over thousands of candidates of FP32 terms of both signs, so one that
+# cancels to almost nothing keeps the rounding of the terms, not of itself.
+CHI2_REL, CHI2_ABS = 1e-4, 6.4e-3
 GRAD_REL = 1e-3
+GRAD_FLOOR = 3e-5
 
 
 @pytest.fixture(scope="module")
@@ -85,8 +89,41 @@ def test_chi2_and_gradient_match_the_oracle(m3e, cfg, ocfg, c4):
         assert s == pytest.approx(tot, rel=1e-4)
         err = np.abs(g - gfd)
         scale = np.abs(gfd[:24]).max()
-        assert err[:24].max() <= GRAD_REL * scale, (err[:24].max() / scale, np.argmax(err[:24]))
+        rel = err[:24] / np.abs(gfd[:24])
+        print("gradient: largest component", scale, "per-component relative error", np.array2string(rel, precision=2),
+              "error / largest", np.array2string(err[:24] / scale, precision=2))
+        bad = err[:24] > GRAD_REL * np.abs(gfd[:24]) + GRAD_FLOOR * scale
+        assert not bad.any(), (np.nonzero(bad)[0], rel[bad], err[:24][bad] / scale)
         assert g[24] == pytest.approx(gfd[24], rel=1e-4)
+
+
+def test_fitted_curvature_matches_the_oracle(m3e, cfg, ocfg, c4):
+    """m3e_fit_kappa: the weighted mean curvature of each candidate's fit at a
+    displaced alignment equals the oracle's fit of the moved FP64 hit positions
+    within 1e-5, and the field scale does not enter it (both triplet weights scale
+    alike; up to rounding)."""
+    d, cand, truth = c4["d"], c4["tm"][:400], c4["truth"]
+    p32 = np.asarray(truth, np.float32).astype(np.float64)
+    with m3e.Context(cfg, 0) as ctx:
+        hits, off, cq, p = _dev(d, cand, truth)
+        k1 = ctx.fit_kappa(hits, off, cq, p).cpu().numpy()
+        p2 = p.clone()
+        p2[24] *= 1.01
+        k2 = ctx.fit_kappa(hits, off, cq, p2).cpu().numpy()
+    assert (np.isnan(k1) == np.isnan(k2)).all()
+    np.testing.assert_allclose(k2[~np.isnan(k1)], k1[~np.isnan(k1)], rtol=1e-6)
+    ref = np.full(cand.shape[0], np.nan)
+    for k, q in enumerate(cand):
+        pos = []
+        for L, h in enumerate(q):
+            hd = O.decode(ocfg, int(d["hits"][h]))
+            pos.append(O.align_point(p32[6 * L:6 * L + 6], [hd.x, hd.y, hd.z]))
+        r = O.fit_track_positions(ocfg, np.array(pos))
+        if r is not None:
+            ref[k] = r[0]
+    ok = np.isfinite(ref)
+    assert ok.mean() > 0.99 and (np.isfinite(k1) == ok).all()
+    np.testing.assert_allclose(k1[ok], ref[ok], rtol=1e-5)
 
 
 def test_gradient_symmetries(m3e, cfg, c4):
