@@ -400,54 +400,80 @@ def align_arm(ctx, gen, m3e, n_frames: int, dev, steps: int = 200) -> dict:
             "field_scale": field_scale_fit(ctx, d, cand, hits, off, est, truth, dev)}
 
 
-def field_scale_fit(ctx, d, cand, hits, off, est, truth, dev) -> dict:
-    """The field scale, which the chi2 sum cannot fix (it grows as the square of the
-    scale), from the energy sum of the signal decays (Sec. "Vertex Fit": the three
-    tracks of mu+ -> e+ e- e+ at rest carry E = m_mu): the decays whose three tracks
-    the selection kept (each a truth-matched candidate), their curvatures from
-    m3e_fit_kappa at the fitted alignment, and the scale s that minimises
-    sum_decays (sum_i sqrt((k B s / |kappa_i|)^2 + m_e^2) - m_mu)^2 (Newton steps in FP64)."""
-    import torch
-    from paper_2206_11535_gb300 import gen as G
-    cfg = G.load_config()
-    kB = cfg["constants"]["k_MeV_per_T_mm"] * cfg["field"]["B_T"]
-    me, mmu = cfg["constants"]["m_e_MeV"], cfg["constants"]["m_mu_MeV"]
+def _signal_decays(d, cand):
+    """Rows of `cand` (kept quadruplets) for the signal decays whose three tracks were all
+    kept, each track by one truth-matched candidate: an (n, 3) index array."""
     trk = d["hit_track"][cand]
     tm = (trk[:, 0] >= 0) & (trk == trk[:, :1]).all(1)
     first = {}
     for k in np.nonzero(tm)[0]:
         first.setdefault(int(trk[k, 0]), k)
-    sig = np.nonzero(d["trk_signal"])[0]
     groups = {}
-    for t in sig:
+    for t in np.nonzero(d["trk_signal"])[0]:
         groups.setdefault(int(d["trk_frame"][t]), []).append(int(t))
-    decays = np.array([[first[t] for t in g] for g in groups.values() if len(g) == 3 and all(t in first for t in g)],
-                      np.int64).reshape(-1, 3)
+    return np.array([[first[t] for t in g] for g in groups.values() if len(g) == 3 and all(t in first for t in g)],
+                    np.int64).reshape(-1, 3)
+
+
+def _energy_scale(ctx, hits, off, cand, decays, params, dev):
+    """The field scale s minimising sum_decays (sum_i sqrt((k B s / |kappa_i|)^2 + m_e^2)
+    - m_mu)^2 (Newton steps in FP64), with the curvatures from m3e_fit_kappa at `params`;
+    returns (s, decays used, its statistical error, rms of the energy sums at s)."""
+    import torch
+    from paper_2206_11535_gb300 import gen as G
+    cfg = G.load_config()
+    kB = cfg["constants"]["k_MeV_per_T_mm"] * cfg["field"]["B_T"]
+    me, mmu = cfg["constants"]["m_e_MeV"], cfg["constants"]["m_mu_MeV"]
+    sub = torch.from_numpy(np.ascontiguousarray(cand[decays.reshape(-1)])).to(dev)
+    k = ctx.fit_kappa(hits, off, sub, torch.tensor(params, dtype=torch.float32, device=dev)).cpu().numpy()
+    p1 = (kB / np.abs(k.astype(np.float64))).reshape(-1, 3)
+    p1 = p1[np.isfinite(p1).all(1)]
+    s = 1.0
+    for _ in range(20):
+        E = np.sqrt((s * p1) ** 2 + me ** 2)
+        r = E.sum(1) - mmu
+        dr = (s * p1 ** 2 / E).sum(1)
+        s -= (r * dr).sum() / (dr * dr).sum()
+    E = np.sqrt((s * p1) ** 2 + me ** 2)
+    r = E.sum(1) - mmu
+    dr = (s * p1 ** 2 / E).sum(1)
+    err = float(np.sqrt((r ** 2).mean() / (dr * dr).sum()))
+    return float(s), int(p1.shape[0]), err, float(np.sqrt((r ** 2).mean()))
+
+
+def field_scale_fit(ctx, d, cand, hits, off, est, truth, dev) -> dict:
+    """The field scale, which the chi2 sum cannot fix (it grows as the square of the
+    scale), from the energy sum of the signal decays (Sec. "Vertex Fit": the three
+    tracks of mu+ -> e+ e- e+ at rest carry E = m_mu): the decays whose three tracks
+    the selection kept, their curvatures from m3e_fit_kappa at the fitted alignment,
+    and the scale that brings their energy sums to m_mu.  The momentum from a fitted
+    curvature, k B s / |kappa|, is biased upward by the curvature's spread, so the raw
+    scale is divided by the raw scale of a calibration sample of the same generator at
+    the nominal field and geometry (seed 1004): the usual simulation-calibrated energy
+    scale."""
+    import torch
+    from paper_2206_11535_gb300 import gen as G
+    decays = _signal_decays(d, cand)
     if decays.shape[0] == 0:
         return {"signal_decays": 0}
-    sub = torch.from_numpy(np.ascontiguousarray(cand[decays.reshape(-1)])).to(dev)
-
-    def solve(params):
-        k = ctx.fit_kappa(hits, off, sub, torch.tensor(params, dtype=torch.float32, device=dev)).cpu().numpy()
-        p1 = (kB / np.abs(k.astype(np.float64))).reshape(-1, 3)
-        ok = np.isfinite(p1).all(1)
-        p1 = p1[ok]
-        s = 1.0
-        for _ in range(20):  # Newton on the sum of squares
-            E = np.sqrt((s * p1) ** 2 + me ** 2)
-            r = E.sum(1) - mmu
-            dr = (s * p1 ** 2 / E).sum(1)
-            s -= (r * dr).sum() / (dr * dr).sum()
-        return float(s), int(ok.sum()), float(np.sqrt(np.mean(r ** 2)))
-
-    s_fit, n, rms = solve(est)
-    s_truth_align, _, _ = solve(truth)
-    s_nominal, _, _ = solve(np.r_[np.zeros(24), 1.0])
-    return {"signal_decays": n, "injected": float(truth[24]), "recovered": s_fit,
-            "residual": s_fit - float(truth[24]), "recovered_at_true_alignment": s_truth_align,
-            "recovered_at_nominal_alignment": s_nominal, "energy_sum_rms_MeV": rms,
-            "method": "energy sum of the signal decays whose three tracks were kept, curvatures from m3e_fit_kappa "
-                      "at the fitted alignment, least squares in the scale"}
+    s_fit, n, err, rms = _energy_scale(ctx, hits, off, cand, decays, est, dev)
+    s_true_align = _energy_scale(ctx, hits, off, cand, decays, truth, dev)[0]
+    # calibration sample: nominal detector and field, the same frame mix
+    dc = G.generate(d["off"].size - 1, 10.0, 0.5, 10, seed=1004)
+    hc, oc = torch.from_numpy(dc["hits"]).to(dev), torch.from_numpy(dc["off"]).to(dev)
+    rec = {k: v.cpu().numpy() for k, v in ctx.select_frames_debug(hc, oc).items()}
+    from paper_2206_11535_gb300 import m3e as M
+    cc = M.kept_candidates(rec, dc["off"])
+    s_cal, n_cal, err_cal, _ = _energy_scale(ctx, hc, oc, cc, _signal_decays(dc, cc), np.r_[np.zeros(24), 1.0], dev)
+    rec_scale = s_fit / s_cal
+    return {"signal_decays": n, "injected": float(truth[24]), "recovered": rec_scale,
+            "residual": rec_scale - float(truth[24]),
+            "statistical_error": float(np.hypot(err / s_cal, err_cal * s_fit / s_cal ** 2)),
+            "recovered_at_true_alignment": s_true_align / s_cal, "raw_scale": s_fit,
+            "calibration_raw_scale": s_cal, "calibration_decays": n_cal, "energy_sum_rms_MeV": rms,
+            "method": "energy sum of the signal decays whose three tracks were kept (curvatures from m3e_fit_kappa "
+                      "at the fitted alignment), least squares in the scale, divided by the same on a nominal "
+                      "calibration sample (seed 1004)"}
 
 
 MU_RATES = (1e8, 2e8, 5e8, 1e9)
