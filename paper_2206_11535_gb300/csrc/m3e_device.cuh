@@ -223,7 +223,7 @@ __device__ __forceinline__ SegF segment_core(float d, float z, float Rct, float 
   const float iph = 1.f / ph, ish = 1.f / sh;
   const float zp = z * iph;
   s.RC = sqrtf(Rct * Rct + zp * zp);
-  s.th = atan2f(Rct * ph, z);
+  s.th = 0.f;  // the polar angle atan2(Rct, zp) itself: computed where it is needed
   const float ish2 = ish * ish;
   s.dphi = -s.RC / (0.125f * d * d * ch * ish2 * ish + zp * zp * iph);
   const float g = 0.5f * ph * ish;
@@ -249,7 +249,9 @@ __device__ __forceinline__ SegF segment(float d, float z, float Rct, float inv2R
     ph = TWO_PI_F - ph;
     ch = -ch;
   }
-  return segment_core(d, z, Rct, sh, ch, ph);
+  SegF s = segment_core(d, z, Rct, sh, ch, ph);
+  s.th = atan2f(Rct * ph, z);
+  return s;
 }
 
 struct TFitF {
@@ -258,7 +260,7 @@ struct TFitF {
   float alpha, a0p, beta, b0p; // Phi_MS ~ alpha u + a0p, Theta_MS ~ beta u + b0p, u = R - Rref
   float s2;                    // sin^2 of the mean polar angle
   float kappa, skappa;
-  float thC0, RC0, dth0;
+  float zp0, RC0, dth0;         // segment 0: z / Phi (theta_C0 = atan2(Rct, zp0)), R_C, dtheta/dR
   float zp1;                   // z / Phi of segment 1 = R_t cot(theta_C1)
   int valid;
 };
@@ -305,10 +307,12 @@ __device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx
   f.alpha = 0.5f * (s0.dphi + s1.dphi);
   f.a0p = 0.5f * s1.dphi * dR;
   f.beta = s1.dth - s0.dth;
-  f.b0p = (s1.th - s0.th) + s1.dth * dR;
-  // polar angles lie in (0, pi): the hardware sine (absolute error ~4e-7 on [-pi, pi])
-  const float sn = __sinf(0.5f * (s0.th + s1.th));
-  f.s2 = sn * sn;
+  // polar angles from cos = zp / R_C, sin = R_t / R_C of each segment: their difference
+  // as one well-conditioned atan2, and sin^2 of their mean from cos(theta0 + theta1)
+  // (the common factor 1 / (R_C0 R_C1) drops out of the atan2)
+  const float R2 = f.Rct * f.Rct;
+  f.b0p = atan2f(f.Rct * (s0.zp - s1.zp), fmaf(s0.zp, s1.zp, R2)) + s1.dth * dR;
+  f.s2 = 0.5f * (1.f - (s0.zp * s1.zp - R2) / (s0.RC * s1.RC));
   const float den = f.alpha * f.alpha * f.s2 + f.beta * f.beta;
   const float u = -(f.alpha * f.a0p * f.s2 + f.beta * f.b0p) / den;
   const float Rs = f.Rref + u;
@@ -317,7 +321,7 @@ __device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx
   f.kappa = f.eps * iRs;
   f.skappa = hl * iRs * iRs * iRs / (kB * sqrtf(den));  // sigma_MS(p*) / sqrt(den) / R*^2
   if (!isfinite(f.kappa) || !isfinite(f.skappa) || !(f.skappa > 0.f)) return f;
-  f.thC0 = s0.th;
+  f.zp0 = s0.zp;
   f.RC0 = s0.RC;
   f.dth0 = s0.dth;
   f.zp1 = s1.zp;
@@ -465,11 +469,11 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   const float pb = C.kB * Rb;
   const float chi2 = kink_chi2(f1, Rb, pb * C.ihl[1]) + kink_chi2(f2, Rb, pb * C.ihl[2]);
   o.chi2 = chi2;
-  o.th01 = f1.thC0 + f1.dth0 * (Rb - f1.RC0);
   if (!isfinite(chi2)) return o;
   o.status = 4;
   if (!(chi2 < C.chi2_trk)) return o;
   o.status = 5;
+  o.th01 = atan2f(f1.Rct, f1.zp0) + f1.dth0 * (Rb - f1.RC0);  // theta01 of a kept track
   // track for the vertex stage: transverse circle of radius R sin(theta01) through
   // the layer-0 and layer-1 hits, centre on the side the track turns to
   float st, ct;
