@@ -270,9 +270,10 @@ struct TFitF {
 // minimum in the 3D radius.  The model is written in u = R - R_C0 so that the
 // small offsets (R_C0 - R_C1, theta_C1 - theta_C0) enter directly instead of as
 // differences of large products; the algebra equals the minimum of
-// [Phi_MS^2 sin^2(theta) + Theta_MS^2] / sigma_MS^2.  Out of line: it runs twice
-// per track, and one copy keeps the kernel's instruction footprint small.
-__device__ __noinline__ TFitF fit_triplet(float ax, float ay, float az, float bx, float by, float bz, float cx,
+// [Phi_MS^2 sin^2(theta) + Theta_MS^2] / sigma_MS^2.  Inlined at both calls of a
+// track: as a call, its 18-float result and the caller's live values went through
+// local memory.
+__device__ __forceinline__ TFitF fit_triplet(float ax, float ay, float az, float bx, float by, float bz, float cx,
                                           float cy, float cz, float hl, float kB) {
   TFitF f;
   f.valid = 0;
@@ -367,14 +368,15 @@ constexpr int SCAN3_MAX = 96;
 struct TrackOut {
   int status, i3;
   float kbar, th01, chi2, mbest;
+  float Rct, zp0, dth0, RC0;  // of the first triplet's fit: what the track record needs besides kbar
 };
 
 // Algorithm 3 for one selected triplet (sorted-hit indices i0, i1, i2): fit,
 // estimate the layer-3 point from the first triplet's circle and the second
 // segment's polar angle, take the closest layer-3 hit ((r3 dphi)^2 + dz^2, ties
 // to the smaller address), fit (h1, h2, h3), weighted mean curvature and chi2 of
-// both triplets at it, chi2 cut.  A kept track is written to slot `slot` of the
-// track arrays by the caller (store_track).
+// both triplets at it, chi2 cut.  The caller turns a kept track (status 5) into
+// its record with track_record.
 //
 // Closest hit: a frame with at most SCAN3_MAX layer-3 hits scans them all (the
 // loads are independent, so their latencies overlap); a larger one visits them
@@ -383,11 +385,12 @@ struct TrackOut {
 // rounded across an edge), so once (r3 * that)^2 exceeds the best metric no
 // farther hit can win: the search returns the same hit as a scan of all hits.
 template <class V>
-__device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int i0, int i1, int i2, float* tr) {
+__device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int i0, int i1, int i2) {
   TrackOut o;
   o.status = 0;
   o.i3 = -1;
   o.kbar = o.th01 = o.chi2 = o.mbest = 0.f;
+  o.Rct = o.zp0 = o.dth0 = o.RC0 = 0.f;
   const float4 p0 = v.pos(i0), p1 = v.pos(i1), p2 = v.pos(i2);
   const float x0 = p0.x, y0 = p0.y, z0 = p0.z;
   const float x1 = p1.x, y1 = p1.y, z1 = p1.z;
@@ -405,13 +408,20 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   const float qx0 = a * ux - hh * uy, qy0 = a * uy + hh * ux;
   const float qx1 = a * ux + hh * uy, qy1 = a * uy - hh * ux;
   // turning angle from h2 to each crossing q in the turning sense: the angle from
-  // (h2 - c) to (q - c) is atan2(cross, dot); clockwise turning decreases it
+  // (h2 - c) to (q - c) is atan2(cross, dot); clockwise turning decreases it.  The
+  // crossing reached first is found without the angles: with (dot, -eps cross) as
+  // the direction of the turn, a turn of less than a half (-eps cross >= 0) comes
+  // before one of more, and within a half the turn of q1 is the smaller one when
+  // the direction of q1 lies clockwise of that of q0 (negative 2D cross product).
+  // Only the chosen turn is evaluated.
   const float wx = x2 - f1.ccx, wy = y2 - f1.ccy;
   const float vx0 = qx0 - f1.ccx, vy0 = qy0 - f1.ccy, vx1 = qx1 - f1.ccx, vy1 = qy1 - f1.ccy;
-  const float al0 = wrap_2pi(-f1.eps * atan2f(wx * vy0 - wy * vx0, wx * vx0 + wy * vy0));
-  const float al1 = wrap_2pi(-f1.eps * atan2f(wx * vy1 - wy * vx1, wx * vx1 + wy * vy1));
-  const bool take1 = al1 < al0;
-  const float al = take1 ? al1 : al0;
+  const float cr0 = wx * vy0 - wy * vx0, dt0 = wx * vx0 + wy * vy0;
+  const float cr1 = wx * vy1 - wy * vx1, dt1 = wx * vx1 + wy * vy1;
+  const float t0 = -f1.eps * cr0, t1 = -f1.eps * cr1;
+  const bool lo0 = !(t0 < 0.f), lo1 = !(t1 < 0.f);
+  const bool take1 = (lo1 && !lo0) || (lo1 == lo0 && dt0 * t1 - t0 * dt1 < 0.f);
+  const float al = wrap_2pi(-f1.eps * atan2f(take1 ? cr1 : cr0, take1 ? dt1 : dt0));
   const float qx = take1 ? qx1 : qx0, qy = take1 ? qy1 : qy0;
   const float z3 = z2 + al * f1.zp1;  // R_t * dPhi * cot(theta_C12)
   float phi3 = atan2f(qy, qx);
@@ -421,12 +431,17 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   int best = -1;
   float mb = FLT_MAX;
   uint32_t ab = 0;
+  // (r3 dphi)^2 + dz^2, rounded in one fixed order wherever it is inlined
+  auto metric = [&](const float4& q) {
+    const float rd = __fmul_rn(r3, wrap_pi(__fsub_rn(q.w, phi3)));
+    const float dz = __fsub_rn(q.z, z3);
+    return __fmaf_rn(rd, rd, __fmul_rn(dz, dz));
+  };
+  // the full rule: an equal metric goes to the smaller address
   auto visit = [&](int j) {
     const float4 q = v.pos(j);
-    const float dphi = wrap_pi(q.w - phi3);
-    const float dz = q.z - z3;
-    const float mm = (r3 * dphi) * (r3 * dphi) + dz * dz;
     const uint32_t aj = v.addr(j);
+    const float mm = metric(q);
     if (best < 0 || mm < mb || (mm == mb && aj < ab)) {
       best = j;
       mb = mm;
@@ -435,9 +450,26 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   };
   const int l3a = v.l3(0), l3e = v.l3(NB);
   if (l3e - l3a <= SCAN3_MAX) {
-    // few layer-3 hits: a straight scan, whose loads do not depend on each other
+    // few layer-3 hits: a straight scan, whose loads do not depend on each other.
+    // It reads no addresses: it notes whether another hit has the same metric as
+    // the best so far, and only then (rarely) repeats the scan with the full rule.
+    bool tie = false;
 #pragma unroll 4
-    for (int j = l3a; j < l3e; ++j) visit(j);
+    for (int j = l3a; j < l3e; ++j) {
+      const float mm = metric(v.pos(j));
+      if (best < 0 || mm < mb) {
+        best = j;
+        mb = mm;
+        tie = false;
+      } else if (mm == mb) {
+        tie = true;
+      }
+    }
+    if (tie) {
+      best = -1;
+      mb = FLT_MAX;
+      for (int j = l3a; j < l3e; ++j) visit(j);
+    }
   } else {
     for (int m = 0; m <= NB / 2; ++m) {
       if (m >= 3) {
@@ -473,12 +505,29 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   o.status = 4;
   if (!(chi2 < C.chi2_trk)) return o;
   o.status = 5;
-  o.th01 = atan2f(f1.Rct, f1.zp0) + f1.dth0 * (Rb - f1.RC0);  // theta01 of a kept track
-  // track for the vertex stage: transverse circle of radius R sin(theta01) through
-  // the layer-0 and layer-1 hits, centre on the side the track turns to
-  float st, ct;
-  __sincosf(o.th01, &st, &ct);  // theta01 in (0, pi), as in fit_triplet
-  const float eps = kb > 0.f ? 1.f : -1.f;
+  o.th01 = atan2f(f1.Rct, f1.zp0) + f1.dth0 * (Rb - f1.RC0);  // theta01 (candidate record)
+  o.Rct = f1.Rct;
+  o.zp0 = f1.zp0;
+  o.dth0 = f1.dth0;
+  o.RC0 = f1.RC0;
+  return o;
+}
+
+// Record of a kept track for the vertex stage (layout below), from the layer-0 and
+// layer-1 hits p0, p1 and the reconstruction o: transverse circle of radius
+// R sin(theta01) through the two hits, centre on the side the track turns to.
+// theta01 = theta_C0 + dtheta/dR (R - R_C0) enters through its cosine and sine,
+// the rotation of (cos, sin) theta_C0 = (zp0, R_t) / R_C0 by the small correction.
+__device__ __forceinline__ void track_record(const float4& p0, const float4& p1, const TrackOut& o, const DevCfg& C,
+                                             float* tr) {
+  const float x0 = p0.x, y0 = p0.y, x1 = p1.x, y1 = p1.y;
+  const float Rb = 1.f / fabsf(o.kbar);
+  const float pb = C.kB * Rb;
+  float sd, cd;
+  __sincosf(o.dth0 * (Rb - o.RC0), &sd, &cd);
+  const float iRC = 1.f / o.RC0;
+  const float ct = (o.zp0 * cd - o.Rct * sd) * iRC, st = (o.Rct * cd + o.zp0 * sd) * iRC;
+  const float eps = o.kbar > 0.f ? 1.f : -1.f;
   const float rt = Rb * st;
   const float dx = x1 - x0, dy = y1 - y0;
   const float d = sqrtf(dx * dx + dy * dy);
@@ -498,10 +547,9 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   tr[8] = C.hl[0] / pb;
   tr[9] = x0;
   tr[10] = y0;
-  tr[11] = z0;
+  tr[11] = p0.z;
   tr[12] = atan2f(y0 - cy, x0 - cx);
   tr[13] = eps;
-  return o;
 }
 
 // Track record layout (16 floats, also the global record of the staged form):
@@ -1305,9 +1353,10 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
   // ---- D: track reconstruction (Algorithm 3), one thread per triplet
   for (int t = g.rank(); t < ntrip; t += G::N) {
     const auto tr = sm.u.trip[t];
-    float tk[14];
-    const TrackOut o = build_track(view, C, tr.x, tr.y, tr.z, tk);
+    const TrackOut o = build_track(view, C, tr.x, tr.y, tr.z);
     if (o.status == 5) {
+      float tk[14];
+      track_record(view.pos(tr.x), view.pos(tr.y), o, C, tk);
       int slot = -1;
       if (tk[13] > 0.f) {
         const int k = atomicAdd(&sm.npos, 1);

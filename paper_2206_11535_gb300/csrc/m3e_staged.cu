@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NT)
 
 // ---- stage 2: one thread per selected triplet
 template <bool DEBUG>
-__global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM: latency hiding over a few spilled registers
+__global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM (72 registers)
     k_stage2(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   const int64_t n = min((int64_t)S.counters[0], S.trip_cap);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -249,10 +249,11 @@ __global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM: latency hiding over
     const int64_t base = (int64_t)(unsigned)r.y;
     const int i0 = r.z & 0xffff, i1 = (int)((unsigned)r.z >> 16), i2 = r.w;
     const GHits v{S.hp + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
-    float tk[14];
-    const TrackOut o = build_track(v, C, i0, i1, i2, tk);
+    const TrackOut o = build_track(v, C, i0, i1, i2);
     S.tstatus[i] = (uint8_t)o.status;
     if (o.status == 5) {
+      float tk[14];
+      track_record(v.pos(i0), v.pos(i1), o, C, tk);
       float4* q = S.trec + 4 * i;
       q[0] = make_float4(tk[0], tk[1], tk[2], tk[3]);
       q[1] = make_float4(tk[4], tk[5], tk[6], tk[7]);

@@ -54,7 +54,11 @@ def _dev(d, cand, params):
 
 
 def test_nominal_chi2_equals_the_selection(m3e, cfg, c4):
-    """At nominal alignment the fit of each kept track gives the selection's chi2."""
+    """At nominal alignment the fit of each kept track gives the selection's chi2.
+    Both kernels inline the same FP32 fit (Sec. "Single Triplet Fit") into different
+    code, where the compiler may fuse different multiply-adds: they agree to a few
+    roundings of its ~100 operations (2e-5 relative; the chi2 band against the
+    FP64 oracle is wider)."""
     d, rec, cand = c4["d"], c4["rec"], c4["cand"]
     with m3e.Context(cfg, 0) as ctx:
         chi2 = ctx.fit_chi2(*_dev(d, cand, O.nominal_params())).cpu().numpy()
@@ -62,7 +66,7 @@ def test_nominal_chi2_equals_the_selection(m3e, cfg, c4):
     st = rec["trk_status"]
     f_idx, t_idx = np.nonzero((np.arange(st.shape[1])[None, :] < np.minimum(rec["n_trip"], st.shape[1])[:, None])
                               & (st >= 5))
-    np.testing.assert_allclose(chi2, rec["trk_val"][f_idx, t_idx, 2], rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(chi2, rec["trk_val"][f_idx, t_idx, 2], rtol=2e-5, atol=1e-6)
 
 
 def test_chi2_and_gradient_match_the_oracle(m3e, cfg, ocfg, c4):
