@@ -74,6 +74,11 @@ struct FrameSm {
   uint8_t p01[CH32 == 1 ? 1 : W_P01];
   uint8_t zbs[CH32 == 1 ? 1 : NZB + 1];
   alignas(16) uint16_t cand[CH32 == 1 ? 1 : W_CAND];  // also the z-bin counters (32-bit words)
+  // CTA stage, selection cuts: the layer-2 hits in z-bin order (sorted-hit indices),
+  // the bin starts of that order and the bin cursors of its counting sort
+  uint16_t zidx[CH32 == 1 ? CH : 1];
+  uint16_t zbs2[CH32 == 1 ? NZB + 1 : 1];
+  uint32_t zcur[CH32 == 1 ? NZB : 1];
   TrkSoA<CK> t;                 // positives from the front, negatives from the back
   union {
     TripT trip[CT];             // selected triplets (sorted-hit indices)
@@ -1262,13 +1267,42 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     if constexpr (G::N == 32) {
       warp_cuts<S, CT>(sm, C, stats, npair, ntt);
     } else {
-      // CTA stage: a warp per layer-1 hit.  The Phi01 window is walked in warp-uniform
-      // steps; for each Phi01 partner the lanes split the Phi12 window, a z window
-      // (the Delta lambda cut seen from the pair, widened by 1e-3 mm) before the exact
-      // tests, which are the warp stage's expressions.  A frame whose triplet count
-      // passed max_trip overflows whatever follows: the warps stop.
+      // CTA stage: a warp per layer-1 hit.  The layer-2 hits are first put in z-bin
+      // order, so that the Delta lambda cut of a (layer-0, layer-1) pair, seen as a z
+      // window on the layer-2 hit (widened by 1e-3 mm against rounding), is one
+      // contiguous range of that order.  The lanes test 32 hits of the Phi01 window at
+      // once; the z ranges of the partners found are numbered by a prefix sum, and the
+      // candidates of all of them are tested 32 at a time (each lane finds its
+      // partner by a search over the lanes' prefix) with the exact Phi12, Delta lambda
+      // and r_tc expressions of the warp stage.  The z window holds every hit that
+      // passes Delta lambda, so the selected set equals the brute-force one.  A frame
+      // whose triplet count passed max_trip overflows whatever follows: the warps stop.
       constexpr int NW = G::N / 32;
       const int lane = g.rank() & 31, wid = g.rank() >> 5;
+      const int l2b = sm.bstart[3 * NB];
+      static_assert(NZB == 64, "two z bins per lane in the prefix sum");
+      for (int k = g.rank(); k < NZB; k += G::N) sm.zcur[k] = 0u;
+      g.sync();
+      for (int i = l1b + g.rank(); i < l2b; i += G::N) atomicAdd(&sm.zcur[zbin2(sm.z[i], C)], 1u);
+      g.sync();
+      if (g.rank() < 32) {
+        const int ca = (int)sm.zcur[2 * lane], cb = (int)sm.zcur[2 * lane + 1];
+        int inc = ca + cb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += t;
+        }
+        const int ex = inc - ca - cb;
+        sm.zbs2[2 * lane] = (uint16_t)ex;
+        sm.zbs2[2 * lane + 1] = (uint16_t)(ex + ca);
+        sm.zcur[2 * lane] = (uint32_t)ex;
+        sm.zcur[2 * lane + 1] = (uint32_t)(ex + ca);
+        if (lane == 31) sm.zbs2[NZB] = (uint16_t)inc;
+      }
+      g.sync();
+      for (int i = l1b + g.rank(); i < l2b; i += G::N) sm.zidx[atomicAdd(&sm.zcur[zbin2(sm.z[i], C)], 1u)] = (uint16_t)i;
+      g.sync();
       auto overflowed = [&]() {
         int ov = 0;
         if (lane == 0) ov = *(volatile int*)&sm.ntrip > C.max_trip;
@@ -1282,48 +1316,65 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
         const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
         const int a0 = sm.bstart[s0], n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
         const int n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
-        const int a2 = sm.bstart[2 * NB + s2], n2a = sm.bstart[2 * NB + min(s2 + nb2, NB)] - a2;
-        const int w2 = sm.bstart[2 * NB];
-        const int n2w = n2a + (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - w2 : 0);
-        if (lane == 0) npair += n0w + n2w;
+        if (stats) {  // the pair tests within the reachable phi bins, and the Phi12 partners
+          const int a2 = sm.bstart[2 * NB + s2], n2a = sm.bstart[2 * NB + min(s2 + nb2, NB)] - a2;
+          const int w2 = sm.bstart[2 * NB];
+          const int n2w = n2a + (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - w2 : 0);
+          if (lane == 0) npair += n0w + n2w;
+        }
         int c12 = 0;  // Phi12 partners of this hit: the candidate count is c01 * c12
         if (stats) {
-          for (int k = lane; k < n2w; k += 32) {
-            const int i2 = k < n2a ? a2 + k : w2 + (k - n2a);
-            c12 += phi_pass(x1, y1, sm.x[i2], sm.y[i2], C.c12);
-          }
+          for (int k = l1b + lane; k < l2b; k += 32) c12 += phi_pass(x1, y1, sm.x[k], sm.y[k], C.c12);
           c12 = (int)__reduce_add_sync(FULL, (unsigned)c12);
         }
         bool stop = false;
         for (int kb = 0; kb < n0w && !stop; kb += 32) {
-          // the lanes test 32 of the Phi01 window at once; the warp walks the partners
           int i0l = 0;
           bool p01 = false;
           if (kb + lane < n0w) {
             i0l = kb + lane < n0a ? a0 + kb + lane : kb + lane - n0a;
             p01 = phi_pass(sm.x[i0l], sm.y[i0l], x1, y1, C.c01);
           }
-          unsigned mp = __ballot_sync(FULL, p01);
+          const unsigned mp = __ballot_sync(FULL, p01);
           if (lane == 0) ntt += __popc(mp) * c12;
-          stop = overflowed();
-          while (mp && !stop) {
-            const int i0 = __shfl_sync(FULL, i0l, __ffs(mp) - 1);
-            mp &= mp - 1;
-            const float x0 = sm.x[i0], y0 = sm.y[i0];
-            const float tl01 = tan_l01(sm.z[i0], z1, C);
+          // the partner's z range in the z order of layer 2
+          float tl01 = 0.f;
+          int lo = 0, cnt = 0;
+          if (p01) {
+            tl01 = tan_l01(sm.z[i0l], z1, C);
             const float zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
             const float zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
-            for (int k = lane; k < n2w; k += 32) {
-              const int i2 = k < n2a ? a2 + k : w2 + (k - n2a);
-              const float z2 = sm.z[i2];
-              if (!(z2 >= zlo && z2 <= zhi)) continue;
-              const float x2 = sm.x[i2], y2 = sm.y[i2];
-              if (!phi_pass(x1, y1, x2, y2, C.c12)) continue;
-              if (!dl_pass(z1, z2, tl01, C)) continue;
-              if (!rtc_pass(x0, y0, x1, y1, x2, y2, C)) continue;
-              const int kk = atomicAdd(&sm.ntrip, 1);
-              if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
+            lo = sm.zbs2[zbin2(zlo, C)];
+            cnt = sm.zbs2[zbin2(zhi, C) + 1] - lo;
+          }
+          int ce = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, ce, o);
+            if (lane >= o) ce += t;
+          }
+          const int pre = ce - cnt, T = __shfl_sync(FULL, ce, 31);
+          for (int e0 = 0; e0 < T && !stop; e0 += 32) {
+            const int e = e0 + lane;
+            int ow = 0;  // the last lane whose candidates start at or before e
+#pragma unroll
+            for (int st = 16; st; st >>= 1) {
+              const int pv = __shfl_sync(FULL, pre, ow + st);
+              if (pv <= e) ow += st;
             }
+            const int i0 = __shfl_sync(FULL, i0l, ow), olo = __shfl_sync(FULL, lo, ow);
+            const int opre = __shfl_sync(FULL, pre, ow);
+            const float ctl = __shfl_sync(FULL, tl01, ow);
+            if (e < T) {
+              const int i2 = sm.zidx[olo + e - opre];
+              const float x2 = sm.x[i2], y2 = sm.y[i2], z2 = sm.z[i2];
+              if (phi_pass(x1, y1, x2, y2, C.c12) && dl_pass(z1, z2, ctl, C) &&
+                  rtc_pass(sm.x[i0], sm.y[i0], x1, y1, x2, y2, C)) {
+                const int kk = atomicAdd(&sm.ntrip, 1);
+                if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
+              }
+            }
+            stop = overflowed();
           }
         }
       }
