@@ -1267,14 +1267,14 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     if constexpr (G::N == 32) {
       warp_cuts<S, CT>(sm, C, stats, npair, ntt);
     } else {
-      // CTA stage: a warp per layer-1 hit.  The layer-2 hits are first put in z-bin
-      // order, so that the Delta lambda cut of a (layer-0, layer-1) pair, seen as a z
-      // window on the layer-2 hit (widened by 1e-3 mm against rounding), is one
-      // contiguous range of that order.  The lanes test 32 hits of the Phi01 window at
-      // once; the z ranges of the partners found are numbered by a prefix sum, and the
-      // candidates of all of them are tested 32 at a time (each lane finds its
-      // partner by a search over the lanes' prefix) with the exact Phi12, Delta lambda
-      // and r_tc expressions of the warp stage.  The z window holds every hit that
+      // CTA stage.  The layer-2 hits are first put in z-bin order, so that the Delta
+      // lambda cut of a (layer-0, layer-1) pair, seen as a z window on the layer-2 hit
+      // (widened by 1e-3 mm against rounding), is one contiguous range of that order.
+      // Each warp holds 32 layer-1 hits at a time and tests the entries of their Phi01
+      // windows 32 at a time (each lane finds its hit by a search over the lanes'
+      // prefix of window sizes); the z ranges of the pairs that pass are numbered by a
+      // prefix sum, and their candidates are tested 32 at a time (a second search)
+      // with the exact Phi12, Delta lambda and r_tc expressions of the warp stage.  The z window holds every hit that
       // passes Delta lambda, so the selected set equals the brute-force one.  A frame
       // whose triplet count passed max_trip overflows whatever follows: the warps stop.
       constexpr int NW = G::N / 32;
@@ -1308,42 +1308,66 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
         if (lane == 0) ov = *(volatile int*)&sm.ntrip > C.max_trip;
         return __shfl_sync(FULL, ov, 0) != 0;
       };
-      for (int i1 = l1a + wid; i1 < l1b; i1 += NW) {
-        if (overflowed()) break;
-        const float x1 = sm.x[i1], y1 = sm.y[i1], z1 = sm.z[i1];
-        const int b1 = layer1_bin(sm.bstart, i1);
-        const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
-        const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
-        const int a0 = sm.bstart[s0], n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
-        const int n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
-        if (stats) {  // the pair tests within the reachable phi bins, and the Phi12 partners
-          const int a2 = sm.bstart[2 * NB + s2], n2a = sm.bstart[2 * NB + min(s2 + nb2, NB)] - a2;
-          const int w2 = sm.bstart[2 * NB];
-          const int n2w = n2a + (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - w2 : 0);
-          if (lane == 0) npair += n0w + n2w;
-        }
-        int c12 = 0;  // Phi12 partners of this hit: the candidate count is c01 * c12
-        if (stats) {
-          for (int k = l1b + lane; k < l2b; k += 32) c12 += phi_pass(x1, y1, sm.x[k], sm.y[k], C.c12);
-          c12 = (int)__reduce_add_sync(FULL, (unsigned)c12);
-        }
-        bool stop = false;
-        for (int kb = 0; kb < n0w && !stop; kb += 32) {
-          int i0l = 0;
-          bool p01 = false;
-          if (kb + lane < n0w) {
-            i0l = kb + lane < n0a ? a0 + kb + lane : kb + lane - n0a;
-            p01 = phi_pass(sm.x[i0l], sm.y[i0l], x1, y1, C.c01);
+      // a warp takes every NW-th layer-1 hit, 32 of them at a time (a lane each);
+      // the Phi01 windows of those hits are tested 32 entries at a time
+      const int nh = l1b - l1a > wid ? (l1b - l1a - wid + NW - 1) / NW : 0;
+      bool stop = false;
+      for (int mb = 0; mb < nh && !stop; mb += 32) {
+        const bool has = mb + lane < nh;
+        const int i1 = l1a + wid + NW * (mb + lane);
+        float x1 = 0.f, y1 = 0.f, z1 = 0.f;
+        int a0 = 0, n0a = 0, n0w = 0, c12 = 0;
+        if (has) {
+          x1 = sm.x[i1];
+          y1 = sm.y[i1];
+          z1 = sm.z[i1];
+          const int b1 = layer1_bin(sm.bstart, i1);
+          const int s0 = nb0 == NB ? 0 : (b1 - C.k01 + NB) & (NB - 1);
+          a0 = sm.bstart[s0];
+          n0a = sm.bstart[min(s0 + nb0, NB)] - a0;
+          n0w = n0a + (s0 + nb0 > NB ? sm.bstart[s0 + nb0 - NB] : 0);
+          if (stats) {  // the pair tests within the reachable phi bins, and the Phi12 partners
+            const int s2 = nb2 == NB ? 0 : (b1 - C.k12 + NB) & (NB - 1);
+            const int a2 = sm.bstart[2 * NB + s2], n2a = sm.bstart[2 * NB + min(s2 + nb2, NB)] - a2;
+            const int w2 = sm.bstart[2 * NB];
+            npair += n0w + n2a + (s2 + nb2 > NB ? sm.bstart[2 * NB + s2 + nb2 - NB] - w2 : 0);
+            for (int k = l1b; k < l2b; ++k) c12 += phi_pass(x1, y1, sm.x[k], sm.y[k], C.c12);
           }
-          const unsigned mp = __ballot_sync(FULL, p01);
-          if (lane == 0) ntt += __popc(mp) * c12;
-          // the partner's z range in the z order of layer 2
+        }
+        int pe = n0w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(FULL, pe, o);
+          if (lane >= o) pe += t;
+        }
+        const int pre1 = pe - n0w, T1 = __shfl_sync(FULL, pe, 31);
+        for (int e0 = 0; e0 < T1 && !stop; e0 += 32) {
+          const int e = e0 + lane;
+          int ow = 0;  // the last lane whose window entries start at or before e
+#pragma unroll
+          for (int st = 16; st; st >>= 1) {
+            const int pv = __shfl_sync(FULL, pre1, ow + st);
+            if (pv <= e) ow += st;
+          }
+          const int oa0 = __shfl_sync(FULL, a0, ow), on0a = __shfl_sync(FULL, n0a, ow);
+          const int opre = __shfl_sync(FULL, pre1, ow), oi1 = __shfl_sync(FULL, i1, ow);
+          const float ox1 = __shfl_sync(FULL, x1, ow), oy1 = __shfl_sync(FULL, y1, ow), oz1 = __shfl_sync(FULL, z1, ow);
+          const int oc12 = __shfl_sync(FULL, c12, ow);
+          int i0 = 0;
+          bool p01 = false;
+          if (e < T1) {
+            const int k = e - opre;
+            i0 = k < on0a ? oa0 + k : k - on0a;
+            p01 = phi_pass(sm.x[i0], sm.y[i0], ox1, oy1, C.c01);
+          }
+          if (p01) ntt += oc12;
+          // the Phi01 pairs' z ranges in the z order of layer 2, then their candidates
           float tl01 = 0.f;
           int lo = 0, cnt = 0;
           if (p01) {
-            tl01 = tan_l01(sm.z[i0l], z1, C);
-            const float zlo = z1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
-            const float zhi = z1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
+            tl01 = tan_l01(sm.z[i0], oz1, C);
+            const float zlo = oz1 + (tl01 - C.dl_max) * C.dr12 - 1e-3f;
+            const float zhi = oz1 + (tl01 + C.dl_max) * C.dr12 + 1e-3f;
             lo = sm.zbs2[zbin2(zlo, C)];
             cnt = sm.zbs2[zbin2(zhi, C) + 1] - lo;
           }
@@ -1353,25 +1377,26 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
             const int t = __shfl_up_sync(FULL, ce, o);
             if (lane >= o) ce += t;
           }
-          const int pre = ce - cnt, T = __shfl_sync(FULL, ce, 31);
-          for (int e0 = 0; e0 < T && !stop; e0 += 32) {
-            const int e = e0 + lane;
-            int ow = 0;  // the last lane whose candidates start at or before e
+          const int pre2 = ce - cnt, T2 = __shfl_sync(FULL, ce, 31);
+          for (int c0 = 0; c0 < T2 && !stop; c0 += 32) {
+            const int c = c0 + lane;
+            int pw = 0;  // the last lane whose candidates start at or before c
 #pragma unroll
             for (int st = 16; st; st >>= 1) {
-              const int pv = __shfl_sync(FULL, pre, ow + st);
-              if (pv <= e) ow += st;
+              const int pv = __shfl_sync(FULL, pre2, pw + st);
+              if (pv <= c) pw += st;
             }
-            const int i0 = __shfl_sync(FULL, i0l, ow), olo = __shfl_sync(FULL, lo, ow);
-            const int opre = __shfl_sync(FULL, pre, ow);
-            const float ctl = __shfl_sync(FULL, tl01, ow);
-            if (e < T) {
-              const int i2 = sm.zidx[olo + e - opre];
+            const int pi0 = __shfl_sync(FULL, i0, pw), pi1 = __shfl_sync(FULL, oi1, pw);
+            const int plo = __shfl_sync(FULL, lo, pw), ppre = __shfl_sync(FULL, pre2, pw);
+            const float ptl = __shfl_sync(FULL, tl01, pw);
+            const float px1 = __shfl_sync(FULL, ox1, pw), py1 = __shfl_sync(FULL, oy1, pw), pz1 = __shfl_sync(FULL, oz1, pw);
+            if (c < T2) {
+              const int i2 = sm.zidx[plo + c - ppre];
               const float x2 = sm.x[i2], y2 = sm.y[i2], z2 = sm.z[i2];
-              if (phi_pass(x1, y1, x2, y2, C.c12) && dl_pass(z1, z2, ctl, C) &&
-                  rtc_pass(sm.x[i0], sm.y[i0], x1, y1, x2, y2, C)) {
+              if (phi_pass(px1, py1, x2, y2, C.c12) && dl_pass(pz1, z2, ptl, C) &&
+                  rtc_pass(sm.x[pi0], sm.y[pi0], px1, py1, x2, y2, C)) {
                 const int kk = atomicAdd(&sm.ntrip, 1);
-                if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(i0, i1, i2);
+                if (kk < CT) sm.u.trip[kk] = make_trip<typename S::TripT>(pi0, pi1, i2);
               }
             }
             stop = overflowed();
