@@ -436,9 +436,13 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   int best = -1;
   float mb = FLT_MAX;
   uint32_t ab = 0;
-  // (r3 dphi)^2 + dz^2, rounded in one fixed order wherever it is inlined
+  // (r3 dphi)^2 + dz^2, rounded in one fixed order wherever it is inlined; dphi is
+  // the difference of the azimuths (both in [0, 2 pi)) less the nearest multiple of
+  // 2 pi, which one fused multiply-add subtracts exactly as a subtraction of 2 pi
+  // would (the two choices at |dphi| = pi give the same metric)
   auto metric = [&](const float4& q) {
-    const float rd = __fmul_rn(r3, wrap_pi(__fsub_rn(q.w, phi3)));
+    const float d = __fsub_rn(q.w, phi3);
+    const float rd = __fmul_rn(r3, __fmaf_rn(-TWO_PI_F, rintf(__fmul_rn(d, 1.f / TWO_PI_F)), d));
     const float dz = __fsub_rn(q.z, z3);
     return __fmaf_rn(rd, rd, __fmul_rn(dz, dz));
   };
@@ -459,10 +463,14 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
     // It reads no addresses: it notes whether another hit has the same metric as
     // the best so far, and only then (rarely) repeats the scan with the full rule.
     bool tie = false;
+    if (l3a < l3e) {
+      best = l3a;
+      mb = metric(v.pos(l3a));
+    }
 #pragma unroll 4
-    for (int j = l3a; j < l3e; ++j) {
+    for (int j = l3a + 1; j < l3e; ++j) {
       const float mm = metric(v.pos(j));
-      if (best < 0 || mm < mb) {
+      if (mm < mb) {
         best = j;
         mb = mm;
         tie = false;
