@@ -506,19 +506,24 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
   const int64_t stride = (int64_t)gridDim.x * S4_WARPS * 32;
   int qn = 0;
   unsigned nv = 0, nvo = 0;
-  for (int64_t base = ((int64_t)blockIdx.x * S4_WARPS + (threadIdx.x >> 5)) * 32;; base += stride) {
+  int64_t base = ((int64_t)blockIdx.x * S4_WARPS + (threadIdx.x >> 5)) * 32;
+  // the combination records are loaded one step ahead; the three circles are read
+  // together with the frame's state, before it is known whether they are needed
+  int4 rn = base + lane < n ? S.combo[base + lane] : make_int4(-1, 0, 0, 0);
+  for (;; base += stride) {
     const bool more = base < n;  // uniform in the warp
     if (more) {
       const int64_t i = base + lane;
+      const int4 r = rn;
+      if (i + stride < n) rn = S.combo[i + stride];
       bool cand = false;
-      if (i < n) {
-        const int4 r = S.combo[i];
+      if (i < n && r.x >= 0) {
         const int f = r.x;
-        if (f >= 0 && S.fstate[f] == PENDING && (DEBUG || !*((volatile int*)S.ffound + f))) {
-          float ca[3], cb[3], ce[3];
-          load_circle(S.trec, r.y, ca[0], ca[1], ca[2]);
-          load_circle(S.trec, r.z, cb[0], cb[1], cb[2]);
-          load_circle(S.trec, r.w, ce[0], ce[1], ce[2]);
+        float ca[3], cb[3], ce[3];
+        load_circle(S.trec, r.y, ca[0], ca[1], ca[2]);
+        load_circle(S.trec, r.z, cb[0], cb[1], cb[2]);
+        load_circle(S.trec, r.w, ce[0], ce[1], ce[2]);
+        if (S.fstate[f] == PENDING && (DEBUG || !*((volatile int*)S.ffound + f))) {
           const int st = vertex_prefilter(ca, cb, ce, C.isect_lim);
           cand = st == 2;
           if (DEBUG && !cand) {  // record the combination with its early status (the same geometry)
