@@ -362,14 +362,18 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
           int cnt = 0, co = 0;
           for (int c = 0; c < nneg; ++c) {
             const bool e_ok = act && fabsf((eab + sm.nE[c]) - C.m_mu) <= C.e_win;
-            const bool open = e_ok && !pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max);
             cnt += e_ok;
-            co += open;
-            const bool wr = prune ? open : e_ok;
-            const unsigned m = __ballot_sync(FULL, wr);
-            const int k = nwrite + __popc(m & ((1u << lane) - 1u));
-            if (wr && k < S3_BUF) sm.wbuf[k] = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)c << 16);
-            nwrite += __popc(m);
+            // few combinations pass the energy window: the P_z test and the write
+            // run only for an e- where one of the warp's pairs passes
+            if (__any_sync(FULL, e_ok)) {
+              const bool open = e_ok && !pz_fails_ptot(__fadd_rn(pzab, sm.nPz[c]), C.ptot_max);
+              co += open;
+              const bool wr = prune ? open : e_ok;
+              const unsigned m = __ballot_sync(FULL, wr);
+              const int k = nwrite + __popc(m & ((1u << lane) - 1u));
+              if (wr && k < S3_BUF) sm.wbuf[k] = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)c << 16);
+              nwrite += __popc(m);
+            }
           }
           ncombo += __reduce_add_sync(FULL, cnt);
           if (stats) nopen += __reduce_add_sync(FULL, co);
