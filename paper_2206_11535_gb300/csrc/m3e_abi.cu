@@ -82,7 +82,7 @@ struct Scratch {
   long long* fcbase = nullptr;              // per frame: first combination
   int64_t frames_cap = 0;
   int4* trip = nullptr;
-  uint8_t* tstatus = nullptr;
+  float2* tek = nullptr;
   float4* trec = nullptr;
   int64_t trip_cap = 0;
   int4* combo = nullptr;
@@ -314,7 +314,7 @@ int ensure_scratch(Scratch& sc, int64_t nf, bool staged) {
   if (tc > sc.trip_cap) {
     int64_t c0 = sc.trip_cap, c1 = sc.trip_cap, c2 = sc.trip_cap;
     rc = grow(sc.trip, c0, tc, sizeof(int4), "triplets");
-    if (!rc) rc = grow(sc.tstatus, c1, tc, 1, "track status");
+    if (!rc) rc = grow(sc.tek, c1, tc, sizeof(float2), "track energies");
     if (!rc) rc = grow(sc.trec, c2, tc, 4 * sizeof(float4), "track records");
     if (rc) return rc;
     sc.trip_cap = tc;
@@ -337,7 +337,7 @@ void free_scratch(Scratch& sc) {
   cudaFree(sc.fint);
   cudaFree(sc.fcbase);
   cudaFree(sc.trip);
-  cudaFree(sc.tstatus);
+  cudaFree(sc.tek);
   cudaFree(sc.trec);
   cudaFree(sc.combo);
   sc = Scratch();
@@ -362,7 +362,7 @@ SParams staged_params(const Scratch& sc) {
   s.lcount = sc.work + 1;
   s.hits_cap = H;
   s.trip = sc.trip;
-  s.tstatus = sc.tstatus;
+  s.tek = sc.tek;
   s.trec = sc.trec;
   s.combo = sc.combo;
   s.counters = sc.counters;

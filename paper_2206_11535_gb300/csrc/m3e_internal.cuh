@@ -93,7 +93,7 @@ struct SParams {
   long long* fcbase;           // per frame: first combination
   int* fncombo;
   int4* trip;                  // {frame, first sorted hit, i0 | i1 << 16, i2} (frame-relative indices), frame -1 = unused
-  uint8_t* tstatus;            // per triplet: track status
+  float2* tek;                 // per triplet: (eps E, P_z) of a kept track, (0, 0) otherwise
   float4* trec;                // per triplet: 16-float track record when kept
   int4* combo;                 // {frame, triplet a, triplet b, triplet e-}, frame -1 = unused
   unsigned long long* counters;  // [0] triplets, [1] combinations, [2] stage-3 queue, [3] sorted hits

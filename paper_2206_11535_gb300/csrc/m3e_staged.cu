@@ -250,16 +250,18 @@ __global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM (72 registers)
     const int i0 = r.z & 0xffff, i1 = (int)((unsigned)r.z >> 16), i2 = r.w;
     const GHits v{S.hp + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
     const TrackOut o = build_track(v, C, i0, i1, i2);
-    S.tstatus[i] = (uint8_t)o.status;
+    float2 te = make_float2(0.f, 0.f);
     if (o.status == 5) {
       float tk[14];
       track_record(v.pos(i0), v.pos(i1), o, C, tk);
+      te = make_float2(tk[13] * tk[7], pz_track(tk[6], tk[4]));  // what the energy test reads
       float4* q = S.trec + 4 * i;
       q[0] = make_float4(tk[0], tk[1], tk[2], tk[3]);
       q[1] = make_float4(tk[4], tk[5], tk[6], tk[7]);
       q[2] = make_float4(tk[8], tk[9], tk[10], tk[11]);
       q[3] = make_float4(tk[12], tk[13], 0.f, 0.f);
     }
+    S.tek[i] = te;
     if (DEBUG) {
       const int t = (int)(i - S.ftbase[f]);
       if (t < P.dump.cap_trip) {
@@ -306,16 +308,10 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
       // kept tracks of the frame's triplets, split by charge
       for (int t0 = 0; t0 < nt; t0 += 32) {
         const int t = t0 + lane;
-        const bool kept = t < nt && S.tstatus[tb + t] == 5;
-        float eps = 0.f, E = 0.f, pz = 0.f;
-        if (kept) {
-          const float4 q1 = __ldg(S.trec + 4 * (int64_t)(tb + t) + 1);
-          const float4 q3 = __ldg(S.trec + 4 * (int64_t)(tb + t) + 3);
-          E = q1.w;
-          pz = pz_track(q1.z, q1.x);
-          eps = q3.y;
-        }
-        const bool pos = kept && eps > 0.f, neg = kept && !(eps > 0.f);
+        // (eps E, P_z) of a kept track (E > 0), (0, 0) for a triplet that made none
+        const float2 te = t < nt ? __ldg(S.tek + tb + t) : make_float2(0.f, 0.f);
+        const float E = fabsf(te.x), pz = te.y;
+        const bool pos = te.x > 0.f, neg = te.x < 0.f;
         const int kp = warp_count_add(&sm.npos, pos);
         const int kn = warp_count_add(&sm.nneg, neg);
         if (pos && kp < C_TRK) {
