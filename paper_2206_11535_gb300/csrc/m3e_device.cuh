@@ -1144,9 +1144,10 @@ constexpr int PENDING = -2;  // frame_front result: triplets selected, later sta
 // the read-only path.
 // prefetch_next: the group takes frame f + 1 next; its addresses are fetched into
 // L1 while this frame is processed.
-template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG, bool LIVE = false>
+// NOST: compiled for runs without statistics (P.stats is null).
+template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG, bool LIVE = false, bool NOST = false>
 __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P, int f, bool prefetch_next = false) {
-  const bool stats = P.stats != nullptr;
+  const bool stats = !NOST && P.stats != nullptr;
   const int64_t base = P.off[f] - P.off_base;
   const int64_t n64 = P.off[f + 1] - P.off[f];
   if constexpr (G::N == 32 && !LIVE) {
@@ -1558,13 +1559,13 @@ __device__ int frame_back(const G& g, S& sm, const DevCfg& C, const KParams& P, 
   return found ? M3E_VERTEX : M3E_DROP;
 }
 
-template <class G, class S>
+template <class G, class S, bool NOST = false>
 __device__ __forceinline__ void finish_frame(const G& g, S& sm, const KParams& P, int f, int r) {
   g.sync();
   if (g.leader()) {
     P.keep[f] = (uint8_t)(r != M3E_DROP);
     P.reason[f] = (uint8_t)r;
-    if (P.stats) {
+    if (!NOST && P.stats) {
       sm.acc[ST_REASON0 + r] += 1;
       for (int k = 0; k < ST_REASON0; ++k) sm.acc[k] += sm.facc[k];
     }

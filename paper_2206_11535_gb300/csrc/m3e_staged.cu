@@ -108,7 +108,7 @@ __device__ __forceinline__ bool emit_frame(const G& g, Sm& sm, const DevCfg& C, 
 }
 
 // After frame_front: decide, emit, or defer one frame (stage-1 tiers).
-template <class G, class Sm, bool DEBUG, bool LIVE = false>
+template <class G, class Sm, bool DEBUG, bool LIVE = false, bool NOST = false>
 __device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const DevCfg& C, const KParams& P, const SParams& S,
                                               int f, int r, long long* bcast) {
   const int ntrip = sm.ntrip;
@@ -116,7 +116,7 @@ __device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const DevCfg& 
   if (r == PENDING) {
     const int n = (int)(P.off[f + 1] - P.off[f]);
     if (emit_frame<G, Sm, DEBUG, LIVE>(g, sm, C, P, S, f, n, ntrip, bcast)) {
-      if (g.leader() && P.stats)
+      if (!NOST && g.leader() && P.stats)
         for (int k = 0; k < ST_REASON0; ++k) sm.acc[k] += sm.facc[k];
     } else {
       r = DEFERRED;
@@ -127,11 +127,11 @@ __device__ __forceinline__ void stage1_finish(const G& g, Sm& sm, const DevCfg& 
       S.fstate[f] = DEFERRED;
       const int k = atomicAdd(P.defer_count, 1);
       P.defer_list[k] = f;
-      if (P.stats) sm.acc[ST_DEFER] += 1;
+      if (!NOST && P.stats) sm.acc[ST_DEFER] += 1;
     }
   } else if (r != PENDING) {
     if (g.leader()) S.fstate[f] = r;
-    finish_frame(g, sm, P, f, r);
+    finish_frame<G, Sm, NOST>(g, sm, P, f, r);
   }
   g.sync();
 }
@@ -173,7 +173,8 @@ __device__ bool gate_wait(const KParams& P, int k) {
 // ---- stage 1, warp tier: one warp per frame, frames from the device queue.
 // GATED (host entry point): the hits arrive while the kernel runs; a frame is
 // taken only after its chunk's arrival flag, and the hits are read past L1.
-template <bool DEBUG, bool GATED = false>
+// NOST: the instance for runs without statistics (no statistics code at all).
+template <bool DEBUG, bool GATED = false, bool NOST = false>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     k_stage1(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -202,11 +203,11 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
           arrived = k;
         }
       }
-      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED>(g, sm, C, P, f, f + 1 < f1);
-      stage1_finish<WarpGroup, Sm, DEBUG, GATED>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
+      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED, NOST>(g, sm, C, P, f, f + 1 < f1);
+      stage1_finish<WarpGroup, Sm, DEBUG, GATED, NOST>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
     }
   }
-  flush_stats(g, sm, P.stats);
+  if (!NOST) flush_stats(g, sm, P.stats);
 }
 
 // ---- stage 1, CTA tiers: one CTA per frame deferred by the tier below (large
@@ -280,8 +281,9 @@ __global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM (72 registers)
   }
 }
 
-// ---- stage 3: warp per frame, track cap and energy test
-template <bool DEBUG>
+// ---- stage 3: warp per frame, track cap and energy test (NOST: the instance for
+// runs without statistics)
+template <bool DEBUG, bool NOST = false>
 __global__ void __launch_bounds__(S3_WARPS * 32)
     k_stage3(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   __shared__ S3Sm smem[S3_WARPS];
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(S3_WARPS * 32)
   for (int k = lane; k < ST_REASON0 + 8; k += 32) sm.acc[k] = 0;
   __syncwarp();
   const int nf = (int)P.n_frames;
-  const bool stats = P.stats != nullptr;
+  const bool stats = !NOST && P.stats != nullptr;
   for (;;) {
     int f0 = 0;
     if (lane == 0) f0 = (int)atomicAdd(&S.counters[2], (unsigned long long)P.grab);
@@ -496,7 +498,7 @@ __device__ __forceinline__ void stage4_dump(const DevCfg& C, const KParams& P, c
   }
 }
 
-template <bool DEBUG>
+template <bool DEBUG, bool NOST = false>
 __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 registers)
     k_stage4(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   __shared__ long long queue[S4_WARPS][64];
@@ -545,7 +547,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
         const TrackR A = load_track(S.trec, r.y), B = load_track(S.trec, r.z), E = load_track(S.trec, r.w);
         const VtxOut v = vertex(A, B, E, C);
         nv += v.status == 2;
-        if (P.stats && v.status == 2)
+        if (!NOST && P.stats && v.status == 2)
           nvo += !pz_fails_ptot(pz_sum(pz_track(A.p, A.ct), pz_track(B.p, B.ct), pz_track(E.p, E.ct)), C.ptot_max);
         if (v.pass) S.ffound[r.x] = 1;
         if (DEBUG) stage4_dump<DEBUG>(C, P, S, i, r, v, A, B, E);
@@ -555,7 +557,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, 8)  // 8 CTAs per SM (64 regist
     }
     if (!more) break;
   }
-  if (P.stats) {
+  if (!NOST && P.stats) {
     const unsigned s = __reduce_add_sync(FULL, nv), so = __reduce_add_sync(FULL, nvo);
     if (lane == 0 && s) atomicAdd(P.stats + ST_VTX, (unsigned long long)s);
     if (lane == 0 && so) atomicAdd(P.stats + ST_VTXOPEN, (unsigned long long)so);
@@ -595,14 +597,15 @@ int stage_blocks_per_sm(int stage) {
   int nb = 0;
   cudaError_t e = cudaSuccess;
   if (stage == 1) {
-    set_smem(k_stage1<false>, stage1_smem_bytes());
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1<false>, WARPS_PER_CTA * 32, stage1_smem_bytes());
+    set_smem(k_stage1<false, false, true>, stage1_smem_bytes());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1<false, false, true>, WARPS_PER_CTA * 32,
+                                                      stage1_smem_bytes());
   } else if (stage == 2) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage2<false>, 128, 0);
   } else if (stage == 3) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage3<false>, S3_WARPS * 32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage3<false, true>, S3_WARPS * 32, 0);
   } else if (stage == 4) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage4<false>, S4_WARPS * 32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage4<false, true>, S4_WARPS * 32, 0);
   } else if (stage == 5) {
     set_smem(k_stage1c<SmFrontCta, C_HITS, false>, stage1c_smem_bytes());
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1c<SmFrontCta, C_HITS, false>, CTA_THREADS,
@@ -637,8 +640,10 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
                           cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1, int mid_threads) {
   const size_t sm1 = stage1_smem_bytes(debug), smc = stage1c_smem_bytes(), smm = stage1m_smem_bytes();
   const bool gated = p.gate != nullptr && !debug;
+  const bool nost = p.stats == nullptr;
   cudaError_t e = debug ? set_smem(k_stage1<true>, sm1)
-                        : (gated ? set_smem(k_stage1<false, true>, sm1) : set_smem(k_stage1<false>, sm1));
+                        : (gated ? set_smem(k_stage1<false, true>, sm1)
+                                 : (nost ? set_smem(k_stage1<false, false, true>, sm1) : set_smem(k_stage1<false>, sm1)));
   if (e == cudaSuccess)
     e = debug ? set_smem(k_stage1c<SmFrontCta, C_HITS, true>, smc) : set_smem(k_stage1c<SmFrontCta, C_HITS, false>, smc);
   if (e == cudaSuccess)
@@ -660,6 +665,7 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   if (ev) cudaEventRecord(ev[0], st);
   if (debug) k_stage1<true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   else if (gated) k_stage1<false, true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
+  else if (nost) k_stage1<false, false, true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   else k_stage1<false><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   // the later kernels read the hits too: order them after every copy of the host entry
   if (after_s1) cudaStreamWaitEvent(st, after_s1, 0);
@@ -685,9 +691,11 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   else k_stage2<false><<<grids[1], 128, 0, st>>>(c, p, s);
   if (ev) cudaEventRecord(ev[4], st);
   if (debug) k_stage3<true><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p3, s);
+  else if (nost) k_stage3<false, true><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p3, s);
   else k_stage3<false><<<grids[2], S3_WARPS * 32, 0, st>>>(c, p3, s);
   if (ev) cudaEventRecord(ev[5], st);
   if (debug) k_stage4<true><<<grids[3], S4_WARPS * 32, 0, st>>>(c, p, s);
+  else if (nost) k_stage4<false, true><<<grids[3], S4_WARPS * 32, 0, st>>>(c, p, s);
   else k_stage4<false><<<grids[3], S4_WARPS * 32, 0, st>>>(c, p, s);
   if (ev) cudaEventRecord(ev[6], st);
   const int g5 = (int)((p.n_frames + 255) / 256);
