@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
 // ---- stage 1, CTA tiers: one CTA per frame deferred by the tier below (large
 // frames); the middle tier stages up to M_HITS hits, the top tier C_HITS.
 // NT: threads of a CTA (the middle tier's is a tuning parameter).
-template <class Sm, int CH, bool DEBUG, int NT = CTA_THREADS>
+template <class Sm, int CH, bool DEBUG, int NT = CTA_THREADS, bool NOST = false>
 __global__ void __launch_bounds__(NT)
     k_stage1c(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -226,10 +226,10 @@ __global__ void __launch_bounds__(NT)
     const int f = P.in_list[i];
     int r;
     if (CH < C_HITS && P.off[f + 1] - P.off[f] > CH) r = DEFERRED;  // for the next tier
-    else r = frame_front<CtaGroup<NT>, Sm, CH, C_TRIP, false, DEBUG>(g, sm, C, P, f);
-    stage1_finish<CtaGroup<NT>, Sm, DEBUG>(g, sm, C, P, S, f, r, bcast);
+    else r = frame_front<CtaGroup<NT>, Sm, CH, C_TRIP, false, DEBUG, false, NOST>(g, sm, C, P, f);
+    stage1_finish<CtaGroup<NT>, Sm, DEBUG, false, NOST>(g, sm, C, P, S, f, r, bcast);
   }
-  flush_stats(g, sm, P.stats);
+  if (!NOST) flush_stats(g, sm, P.stats);
 }
 
 // ---- stage 2: one thread per selected triplet
@@ -607,12 +607,12 @@ int stage_blocks_per_sm(int stage) {
   } else if (stage == 4) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage4<false, true>, S4_WARPS * 32, 0);
   } else if (stage == 5) {
-    set_smem(k_stage1c<SmFrontCta, C_HITS, false>, stage1c_smem_bytes());
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1c<SmFrontCta, C_HITS, false>, CTA_THREADS,
+    set_smem(k_stage1c<SmFrontCta, C_HITS, false, CTA_THREADS, true>, stage1c_smem_bytes());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1c<SmFrontCta, C_HITS, false, CTA_THREADS, true>, CTA_THREADS,
                                                       stage1c_smem_bytes());
   } else {
-    set_smem(k_stage1c<SmFrontMid, M_HITS, false>, stage1m_smem_bytes());
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1c<SmFrontMid, M_HITS, false>, CTA_THREADS,
+    set_smem(k_stage1c<SmFrontMid, M_HITS, false, CTA_THREADS, true>, stage1m_smem_bytes());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage1c<SmFrontMid, M_HITS, false, CTA_THREADS, true>, CTA_THREADS,
                                                       stage1m_smem_bytes());
   }
   return e == cudaSuccess && nb > 0 ? nb : 1;
@@ -621,9 +621,9 @@ int stage_blocks_per_sm(int stage) {
 template <int NT>
 int mid_blocks_per_sm_t() {
   int nb = 0;
-  set_smem(k_stage1c<SmFrontMid, M_HITS, false, NT>, stage1m_smem_bytes());
+  set_smem(k_stage1c<SmFrontMid, M_HITS, false, NT, true>, stage1m_smem_bytes());
   const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &nb, k_stage1c<SmFrontMid, M_HITS, false, NT>, NT, stage1m_smem_bytes());
+      &nb, k_stage1c<SmFrontMid, M_HITS, false, NT, true>, NT, stage1m_smem_bytes());
   return e == cudaSuccess && nb > 0 ? nb : 1;
 }
 
@@ -636,6 +636,22 @@ int stage1_mid_blocks_per_sm(int threads) {
 // 4, stage 1 top tier, stage 1 middle tier.  Frames deferred by the top tier or by
 // stage 3 end up in S.list2 for the caller's CTA-per-frame kernel.  ev (9 events or
 // null): before stage 1 and after each kernel.
+// One launch of a CTA tier of stage 1 (the instance without statistics code when nost).
+template <class Sm, int CH, bool DEBUG, int NT>
+cudaError_t launch_tier(const DevCfg& c, const KParams& p, const SParams& s, int grid, size_t smem, cudaStream_t st,
+                        bool nost) {
+  if constexpr (!DEBUG) {
+    if (nost) {
+      const cudaError_t e = set_smem(k_stage1c<Sm, CH, false, NT, true>, smem);
+      if (e == cudaSuccess) k_stage1c<Sm, CH, false, NT, true><<<grid, NT, smem, st>>>(c, p, s);
+      return e;
+    }
+  }
+  const cudaError_t e = set_smem(k_stage1c<Sm, CH, DEBUG, NT>, smem);
+  if (e == cudaSuccess) k_stage1c<Sm, CH, DEBUG, NT><<<grid, NT, smem, st>>>(c, p, s);
+  return e;
+}
+
 cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, const int grids[6], bool debug,
                           cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_s1, int mid_threads) {
   const size_t sm1 = stage1_smem_bytes(debug), smc = stage1c_smem_bytes(), smm = stage1m_smem_bytes();
@@ -644,10 +660,6 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   cudaError_t e = debug ? set_smem(k_stage1<true>, sm1)
                         : (gated ? set_smem(k_stage1<false, true>, sm1)
                                  : (nost ? set_smem(k_stage1<false, false, true>, sm1) : set_smem(k_stage1<false>, sm1)));
-  if (e == cudaSuccess)
-    e = debug ? set_smem(k_stage1c<SmFrontCta, C_HITS, true>, smc) : set_smem(k_stage1c<SmFrontCta, C_HITS, false>, smc);
-  if (e == cudaSuccess)
-    e = debug ? set_smem(k_stage1c<SmFrontMid, M_HITS, true>, smm) : set_smem(k_stage1c<SmFrontMid, M_HITS, false>, smm);
   if (e != cudaSuccess) return e;
   KParams p1 = p, pm = p, pc = p, p3 = p;
   p1.defer_list = s.list1;
@@ -670,22 +682,15 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   // the later kernels read the hits too: order them after every copy of the host entry
   if (after_s1) cudaStreamWaitEvent(st, after_s1, 0);
   if (ev) cudaEventRecord(ev[1], st);
-  if (debug) {
-    k_stage1c<SmFrontMid, M_HITS, true><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
-  } else if (mid_threads == 128) {
-    e = set_smem(k_stage1c<SmFrontMid, M_HITS, false, 128>, smm);
-    if (e != cudaSuccess) return e;
-    k_stage1c<SmFrontMid, M_HITS, false, 128><<<grids[5], 128, smm, st>>>(c, pm, s);
-  } else if (mid_threads == 512) {
-    e = set_smem(k_stage1c<SmFrontMid, M_HITS, false, 512>, smm);
-    if (e != cudaSuccess) return e;
-    k_stage1c<SmFrontMid, M_HITS, false, 512><<<grids[5], 512, smm, st>>>(c, pm, s);
-  } else {
-    k_stage1c<SmFrontMid, M_HITS, false><<<grids[5], CTA_THREADS, smm, st>>>(c, pm, s);
-  }
+  e = debug ? launch_tier<SmFrontMid, M_HITS, true, CTA_THREADS>(c, pm, s, grids[5], smm, st, false)
+            : mid_threads == 128 ? launch_tier<SmFrontMid, M_HITS, false, 128>(c, pm, s, grids[5], smm, st, nost)
+            : mid_threads == 512 ? launch_tier<SmFrontMid, M_HITS, false, 512>(c, pm, s, grids[5], smm, st, nost)
+                                 : launch_tier<SmFrontMid, M_HITS, false, CTA_THREADS>(c, pm, s, grids[5], smm, st, nost);
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], st);
-  if (debug) k_stage1c<SmFrontCta, C_HITS, true><<<grids[4], CTA_THREADS, smc, st>>>(c, pc, s);
-  else k_stage1c<SmFrontCta, C_HITS, false><<<grids[4], CTA_THREADS, smc, st>>>(c, pc, s);
+  e = debug ? launch_tier<SmFrontCta, C_HITS, true, CTA_THREADS>(c, pc, s, grids[4], smc, st, false)
+            : launch_tier<SmFrontCta, C_HITS, false, CTA_THREADS>(c, pc, s, grids[4], smc, st, nost);
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], st);
   if (debug) k_stage2<true><<<grids[1], 128, 0, st>>>(c, p, s);
   else k_stage2<false><<<grids[1], 128, 0, st>>>(c, p, s);
