@@ -26,13 +26,13 @@ the largest one grew with the sample, which is why the margin is wide.
   energy        energy window                            3.1e-5         2e-4
   vtx_chi2      vertex chi2 cut                          3.0e-4         2e-3
   tdist         target-distance cut                      5.2e-3         3e-2
-  ptot          |sum p| cut                              4.4e-5         2e-4
+  ptot          |sum p| cut                              4.5e-5         2e-4
   disc          |h^2| / (r_a r_b) of a circle pair       1.6e-3         7e-3
-  filter        mm, | |point| - filter radius |          4.3e-3         2e-2
+  filter        mm, | |point| - filter radius |          6.7e-3         3e-2
   choice        1 + chi2, on chi2_second - chi2          3.5e-3         2e-2
 
 Values of matched candidates: the fitted curvature and polar angle within 1e-5
-relative (largest differences 2.5e-6 and 7.2e-7); the chi2 of a kept track within
+relative (largest differences 2.6e-6 and 7.2e-7); the chi2 of a kept track within
 the chi2_track band; vertex values within band x threshold + VAL_REL x value
 (far from the threshold, largest relative differences 1.7e-3, 7.6e-4 and 6.9e-5
 for the vertex chi2, the target distance and |sum p|).
@@ -52,7 +52,7 @@ from oracle import oracle as O
 
 # boundary bands (see the table above)
 BAND = dict(selection=1e-5, chi2_track=2e-4, fourth_hit=6e-2, energy=2e-4, vtx_chi2=2e-3, tdist=3e-2, ptot=2e-4,
-            disc=7e-3, filter=2e-2, choice=2e-2)
+            disc=7e-3, filter=3e-2, choice=2e-2)
 # values of matched candidates: fitted curvature and polar angle, relative
 KAPPA_REL = 1e-5
 THETA_REL = 1e-5
