@@ -351,16 +351,61 @@ __device__ __forceinline__ float kink_chi2(const TFitF& f, float R, float isg) {
 // pos(i) = (x, y, z, phi) of sorted hit i.
 template <class S>
 struct SmHits {
+  static constexpr bool kPark = false;
   const S& s;
   __device__ __forceinline__ float4 pos(int i) const { return make_float4(s.x[i], s.y[i], s.z[i], s.phi[i]); }
   __device__ __forceinline__ uint32_t addr(int i) const { return s.addr[i]; }
   __device__ __forceinline__ int l3(int b) const { return s.bstart[3 * NB + b]; }  // layer-3 bin starts
 };
 
+// The first triplet fit's values that the global fit and the track record need,
+// parked in shared memory across the layer-3 search and the second fit (staged form,
+// one slot per thread of a 128-thread CTA): fewer live registers in the track stage.
+struct FitPark {
+  float v[11][128];
+};
+
+__device__ __forceinline__ void park_fit(FitPark& pk, const TFitF& f) {
+  volatile float* q = &pk.v[0][threadIdx.x & 127];
+  q[0 * 128] = f.skappa;
+  q[1 * 128] = f.kappa;
+  q[2 * 128] = f.alpha;
+  q[3 * 128] = f.a0p;
+  q[4 * 128] = f.beta;
+  q[5 * 128] = f.b0p;
+  q[6 * 128] = f.s2;
+  q[7 * 128] = f.Rref;
+  q[8 * 128] = f.Rct;
+  q[9 * 128] = f.zp0;
+  q[10 * 128] = f.dth0;
+}
+
+__device__ __forceinline__ TFitF unpark_fit(const FitPark& pk) {
+  const volatile float* q = &pk.v[0][threadIdx.x & 127];
+  TFitF f;
+  f.skappa = q[0 * 128];
+  f.kappa = q[1 * 128];
+  f.alpha = q[2 * 128];
+  f.a0p = q[3 * 128];
+  f.beta = q[4 * 128];
+  f.b0p = q[5 * 128];
+  f.s2 = q[6 * 128];
+  f.Rref = q[7 * 128];
+  f.Rct = q[8 * 128];
+  f.zp0 = q[9 * 128];
+  f.dth0 = q[10 * 128];
+  f.RC0 = f.Rref;  // R_C of segment 0 is the expansion point
+  f.eps = f.ccx = f.ccy = f.zp1 = 0.f;
+  f.valid = 1;
+  return f;
+}
+
 struct GHits {                       // one 16-byte load per hit
+  static constexpr bool kPark = true;
   const float4* __restrict__ ps;
   const uint32_t* __restrict__ as;
   const uint16_t* __restrict__ l3s;  // NB + 1 layer-3 bin starts, frame-relative
+  FitPark* park;
   __device__ __forceinline__ float4 pos(int i) const { return __ldg(ps + i); }
   __device__ __forceinline__ uint32_t addr(int i) const { return __ldg(as + i); }
   __device__ __forceinline__ int l3(int b) const { return __ldg(l3s + b); }
@@ -375,6 +420,29 @@ struct TrackOut {
   float kbar, th01, chi2, mbest;
   float Rct, zp0, dth0, RC0;  // of the first triplet's fit: what the track record needs besides kbar
 };
+
+// Global fit of a track from its two triplet fits (weighted mean curvature, chi2 of
+// both kink models at it, chi2 cut) and what the track record needs.
+__device__ __forceinline__ TrackOut global_fit(TrackOut o, const TFitF& f1, const TFitF& f2, const DevCfg& C) {
+  const float w1 = 1.f / (f1.skappa * f1.skappa), w2 = 1.f / (f2.skappa * f2.skappa);
+  const float kb = (f1.kappa * w1 + f2.kappa * w2) / (w1 + w2);
+  o.kbar = kb;
+  if (!(kb != 0.f) || !isfinite(kb)) return o;
+  const float Rb = 1.f / fabsf(kb);
+  const float pb = C.kB * Rb;
+  const float chi2 = kink_chi2(f1, Rb, pb * C.ihl[1]) + kink_chi2(f2, Rb, pb * C.ihl[2]);
+  o.chi2 = chi2;
+  if (!isfinite(chi2)) return o;
+  o.status = 4;
+  if (!(chi2 < C.chi2_trk)) return o;
+  o.status = 5;
+  o.th01 = atan2f(f1.Rct, f1.zp0) + f1.dth0 * (Rb - f1.RC0);  // theta01 (candidate record)
+  o.Rct = f1.Rct;
+  o.zp0 = f1.zp0;
+  o.dth0 = f1.dth0;
+  o.RC0 = f1.RC0;
+  return o;
+}
 
 // Algorithm 3 for one selected triplet (sorted-hit indices i0, i1, i2): fit,
 // estimate the layer-3 point from the first triplet's circle and the second
@@ -402,6 +470,7 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   const float x2 = p2.x, y2 = p2.y, z2 = p2.z;
   const TFitF f1 = fit_triplet(x0, y0, z0, x1, y1, z1, x2, y2, z2, C.hl[1], C.kB);
   if (!f1.valid) return o;
+  if constexpr (V::kPark) park_fit(*v.park, f1);
   const float r3 = C.r3;
   const float D = sqrtf(f1.ccx * f1.ccx + f1.ccy * f1.ccy);
   o.status = 1;
@@ -506,25 +575,10 @@ __device__ __forceinline__ TrackOut build_track(const V& v, const DevCfg& C, int
   const TFitF f2 = fit_triplet(x1, y1, z1, x2, y2, z2, p3.x, p3.y, p3.z, C.hl[2], C.kB);
   o.status = 3;
   if (!f2.valid) return o;
-  const float w1 = 1.f / (f1.skappa * f1.skappa), w2 = 1.f / (f2.skappa * f2.skappa);
-  const float kb = (f1.kappa * w1 + f2.kappa * w2) / (w1 + w2);
-  o.kbar = kb;
-  if (!(kb != 0.f) || !isfinite(kb)) return o;
-  const float Rb = 1.f / fabsf(kb);
-  const float pb = C.kB * Rb;
-  const float chi2 = kink_chi2(f1, Rb, pb * C.ihl[1]) + kink_chi2(f2, Rb, pb * C.ihl[2]);
-  o.chi2 = chi2;
-  if (!isfinite(chi2)) return o;
-  o.status = 4;
-  if (!(chi2 < C.chi2_trk)) return o;
-  o.status = 5;
-  o.th01 = atan2f(f1.Rct, f1.zp0) + f1.dth0 * (Rb - f1.RC0);  // theta01 (candidate record)
-  o.Rct = f1.Rct;
-  o.zp0 = f1.zp0;
-  o.dth0 = f1.dth0;
-  o.RC0 = f1.RC0;
-  return o;
+  if constexpr (V::kPark) return global_fit(o, unpark_fit(*v.park), f2, C);
+  else return global_fit(o, f1, f2, C);
 }
+
 
 // Record of a kept track for the vertex stage (layout below), from the layer-0 and
 // layer-1 hits p0, p1 and the reconstruction o: transverse circle of radius

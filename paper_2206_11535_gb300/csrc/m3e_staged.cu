@@ -234,8 +234,10 @@ __global__ void __launch_bounds__(NT)
 
 // ---- stage 2: one thread per selected triplet
 template <bool DEBUG>
-__global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM (72 registers)
+__global__ void __launch_bounds__(128, 8)  // 8 CTAs per SM (64 registers: the first fit parked in shared memory)
     k_stage2(const __grid_constant__ DevCfg C, const __grid_constant__ KParams P, const __grid_constant__ SParams S) {
+  static_assert(sizeof(FitPark) == 11 * 128 * sizeof(float), "one slot per thread of a 128-thread CTA");
+  __shared__ FitPark park;
   const int64_t n = min((int64_t)S.counters[0], S.trip_cap);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(128, 7)  // 7 CTAs per SM (72 registers)
     if (f < 0) continue;
     const int64_t base = (int64_t)(unsigned)r.y;
     const int i0 = r.z & 0xffff, i1 = (int)((unsigned)r.z >> 16), i2 = r.w;
-    const GHits v{S.hp + base, S.haddr + base, S.l3 + (int64_t)f * NL3};
+    const GHits v{S.hp + base, S.haddr + base, S.l3 + (int64_t)f * NL3, &park};
     const TrackOut o = build_track(v, C, i0, i1, i2);
     float2 te = make_float2(0.f, 0.f);
     if (o.status == 5) {
