@@ -660,8 +660,8 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   const bool gated = p.gate != nullptr && !debug;
   const bool nost = p.stats == nullptr;
   cudaError_t e = debug ? set_smem(k_stage1<true>, sm1)
-                        : (gated ? set_smem(k_stage1<false, true>, sm1)
-                                 : (nost ? set_smem(k_stage1<false, false, true>, sm1) : set_smem(k_stage1<false>, sm1)));
+                  : gated ? (nost ? set_smem(k_stage1<false, true, true>, sm1) : set_smem(k_stage1<false, true>, sm1))
+                          : (nost ? set_smem(k_stage1<false, false, true>, sm1) : set_smem(k_stage1<false>, sm1));
   if (e != cudaSuccess) return e;
   KParams p1 = p, pm = p, pc = p, p3 = p;
   p1.defer_list = s.list1;
@@ -678,6 +678,7 @@ cudaError_t launch_staged(const DevCfg& c, const KParams& p, const SParams& s, c
   p3.defer_count = s.lcount + 1;
   if (ev) cudaEventRecord(ev[0], st);
   if (debug) k_stage1<true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
+  else if (gated && nost) k_stage1<false, true, true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   else if (gated) k_stage1<false, true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   else if (nost) k_stage1<false, false, true><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
   else k_stage1<false><<<grids[0], WARPS_PER_CTA * 32, sm1, st>>>(c, p1, s);
