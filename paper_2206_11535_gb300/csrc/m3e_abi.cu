@@ -193,6 +193,10 @@ void make_devcfg(const m3e_config& c, DevCfg& d) {
     d.pk_nrow |= (unsigned long long)d.nrow[L] << (16 * L);
     d.pk_coloff |= (unsigned long long)d.col_off[L] << (16 * L);
     d.pk_rowoff |= (unsigned long long)d.row_off[L] << (16 * L);
+    uint32_t ib;
+    std::memcpy(&ib, &d.intot[L], 4);
+    d.ltab[L] = make_uint4((uint32_t)d.nlad[L] | (uint32_t)d.ncol[L] << 6 | (uint32_t)d.nrow[L] << 15,
+                           (uint32_t)d.col_off[L], (uint32_t)d.row_off[L], ib);
   }
   d.inv_dr01 = (float)(1.0 / (c.r_mm[1] - c.r_mm[0]));
   d.inv_dr12 = (float)(1.0 / (c.r_mm[2] - c.r_mm[1]));

@@ -149,6 +149,24 @@ __device__ __forceinline__ Dec decode(const DevCfg& C, uint32_t a) {
   return d;
 }
 
+// decode() with the per-layer constants from the 16-byte entries of a table in shared
+// memory (DevCfg::ltab): one load per hit, where the constant cache would serialise
+// the loads of a warp's several layers.  The same values as decode().
+__device__ __forceinline__ Dec decode_s(const uint4* tab, uint32_t a) {
+  Dec d;
+  d.L = (a >> 26) & 3;
+  const uint4 t = tab[d.L];
+  const int lad = (a >> 21) & 31, col = (a >> 13) & 255;
+  d.row = a & 8191;
+  const int nlad = (int)(t.x & 63u), ncol = (int)((t.x >> 6) & 511u), nrow = (int)(t.x >> 15);
+  d.ok = (a >> 28) == 0 && lad < nlad && col < ncol && d.row < nrow;
+  d.g = lad * ncol + col;
+  d.ci = (int)t.y + d.g;
+  d.ri = (int)t.z + d.row;
+  d.b = d.ok ? (int)__fmul_rn(__fadd_rn((float)(d.g * NB), 0.5f), __uint_as_float(t.w)) : 0;
+  return d;
+}
+
 // decode without the phi bin and without loads indexed by the hit's layer: the
 // per-layer integers come from packed 16-bit fields.  For a kernel that does little
 // else per hit (the ingest), where loads of per-layer constants at the warp's
@@ -1225,6 +1243,13 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
 
   // ---- A: decode and histogram
   for (int k = g.rank(); k < (S::kPackB ? NBK / 4 : NBK); k += G::N) sm.bcur[k] = 0;
+  // warp stage: the per-layer decode table (DevCfg::ltab) for parts A and B, in the
+  // space of the layer-2 z order, which part C fills later
+  uint4* const ltab = reinterpret_cast<uint4*>(sm.zq);
+  if constexpr (G::N == 32 && DEFER) {
+    static_assert(sizeof(sm.zq) >= 4 * sizeof(uint4), "room for the decode table");
+    if (g.rank() < 4) ltab[g.rank()] = C.ltab[g.rank()];
+  }
   if (g.leader()) {
     sm.bad = 0;
     sm.ntrip = 0;
@@ -1252,7 +1277,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (lane + 32 * k < n) {
-        const Dec d = decode(C, av[k]);
+        const Dec d = decode_s(ltab, av[k]);
         if (!d.ok) bad = true;
         else bucket_add(sm, d.L * NB + d.b);
       }
@@ -1273,7 +1298,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     for (int k = 0; k < K; ++k) {
       const int i = lane + 32 * k;
       if (i < n) {
-        const Dec d = decode(C, av[k]);
+        const Dec d = decode_s(ltab, av[k]);
         const int pos = bucket_add(sm, d.L * NB + d.b);
         const float* cl = reinterpret_cast<const float*>(P.col_lut + d.ci);
         cp_async4(&sm.x[pos], cl);

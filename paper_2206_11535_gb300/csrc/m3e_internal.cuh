@@ -42,6 +42,9 @@ struct DevCfg {
   // the same per-layer integers packed as 16-bit fields (layer L in bits 16 L ..), read
   // by decode with shifts instead of loads indexed by the hit's layer
   unsigned long long pk_nlad, pk_ncol, pk_nrow, pk_coloff, pk_rowoff;
+  // the decode constants of layer L in one 16-byte entry, copied to shared memory by
+  // the selection kernels: {nlad | ncol << 6 | nrow << 15, col_off, row_off, 1/ntot bits}
+  uint4 ltab[4];
   float kB;                   // p [MeV] = kB * R [mm]
   float hl[4];                // Highland width numerator: sigma_MS(p) = hl[layer] / p
   float ihl[4];               // 1 / hl
