@@ -1216,8 +1216,12 @@ constexpr int PENDING = -2;  // frame_front result: triplets selected, later sta
 // the read-only path.
 // prefetch_next: the group takes frame f + 1 next; its addresses are fetched into
 // L1 while this frame is processed.
-// NOST: compiled for runs without statistics (P.stats is null).
-template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG, bool LIVE = false, bool NOST = false>
+// NOST: compiled for runs without statistics (P.stats is null).  TAB: the warp stage
+// decodes with the per-layer constants from a shared-memory table (decode_s) instead of
+// the constant cache (the staged form's stage 1 measured faster so, the fused kernels
+// slower).
+template <class G, class S, int CH, int CT, bool DEFER, bool DEBUG, bool LIVE = false, bool NOST = false,
+          bool TAB = false>
 __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P, int f, bool prefetch_next = false) {
   const bool stats = !NOST && P.stats != nullptr;
   const int64_t base = P.off[f] - P.off_base;
@@ -1246,7 +1250,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
   // warp stage: the per-layer decode table (DevCfg::ltab) for parts A and B, in the
   // space of the layer-2 z order, which part C fills later
   uint4* const ltab = reinterpret_cast<uint4*>(sm.zq);
-  if constexpr (G::N == 32 && DEFER) {
+  if constexpr (G::N == 32 && DEFER && TAB) {
     static_assert(sizeof(sm.zq) >= 4 * sizeof(uint4), "room for the decode table");
     if (g.rank() < 4) ltab[g.rank()] = C.ltab[g.rank()];
   }
@@ -1277,7 +1281,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (lane + 32 * k < n) {
-        const Dec d = decode_s(ltab, av[k]);
+        const Dec d = TAB ? decode_s(ltab, av[k]) : decode(C, av[k]);
         if (!d.ok) bad = true;
         else bucket_add(sm, d.L * NB + d.b);
       }
@@ -1298,7 +1302,7 @@ __device__ int frame_front(const G& g, S& sm, const DevCfg& C, const KParams& P,
     for (int k = 0; k < K; ++k) {
       const int i = lane + 32 * k;
       if (i < n) {
-        const Dec d = decode_s(ltab, av[k]);
+        const Dec d = TAB ? decode_s(ltab, av[k]) : decode(C, av[k]);
         const int pos = bucket_add(sm, d.L * NB + d.b);
         const float* cl = reinterpret_cast<const float*>(P.col_lut + d.ci);
         cp_async4(&sm.x[pos], cl);

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
           arrived = k;
         }
       }
-      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED, NOST>(g, sm, C, P, f, f + 1 < f1);
+      const int r = frame_front<WarpGroup, Sm, W_HITS, S1_TRIP, true, DEBUG, GATED, NOST, true>(g, sm, C, P, f, f + 1 < f1);
       stage1_finish<WarpGroup, Sm, DEBUG, GATED, NOST>(g, sm, C, P, S, f, r, bcast[threadIdx.x >> 5]);
     }
   }
